@@ -1,0 +1,249 @@
+/*
+ * bkfac.h -- C ABI of libbkfac, the GB300 (sm_103a) B-KFAC preconditioning
+ * hot path.
+ *
+ * Paper: "Brand New K-FACs: Speeding up K-FAC with Online Decomposition
+ * Updates", arXiv 2210.08494.
+ *
+ * The library keeps each exponentially averaged (EA) Kronecker factor of an FC
+ * layer (Eq. (5)) as a low-rank eigendecomposition U diag(sigma) U^T and
+ *   - updates it with a new batch of columns X by the symmetric Brand update
+ *     (Algorithm 3) as used by B-KFAC (Algorithm 4, Sec. 3.1):
+ *       K = rho * U diag(sigma) U^T + (1 - rho)/n * X X^T,
+ *       (U, sigma) <- top-r eigenpairs of K;
+ *   - applies the damped inverse of both factors of a layer to its weight
+ *     gradient (Algorithm 1, inverse application; K-FAC identity of Eq. (4)):
+ *       S = (Gamma + lam_G I)^-1 G (A + lam_A I)^-1.
+ *
+ * Conventions
+ *   - Every pointer documented as "device" must point to memory of the
+ *     current CUDA device; "host" pointers are read during the call only.
+ *   - Calls are asynchronous on the caller's stream (NULL = legacy default
+ *     stream).  Argument errors are returned immediately and enqueue nothing.
+ *     Errors found on the device (non-convergence, non-finite data, a
+ *     Cholesky breakdown) are written to a per-device status word that
+ *     bkfac_status() returns; kernels never trap.
+ *   - The per-factor calls allocate no memory: the caller passes a workspace
+ *     of at least the size the matching *_workspace_size() function returns,
+ *     256-byte aligned.  Workspace contents need not be initialised and are
+ *     not meaningful after the call.  Two calls that run concurrently must not
+ *     share a workspace.
+ *   - Matrices: a "d x m column-major" matrix with leading dimension ld stores
+ *     element (i, j) at p[i + j*ld]; this is exactly a row-major torch tensor
+ *     of shape (m, ld) viewed as m columns.  The gradient G and the step S are
+ *     "d_out x d_in row-major" (element (i, j) at p[i*ld + j]), the layout of
+ *     torch's weight.grad with the bias column appended last.
+ *   - Leading dimensions must be >= the row count and a multiple of 4
+ *     elements (16 bytes for FP32) so rows can be read with vector loads;
+ *     base pointers must be 16-byte aligned.
+ */
+#ifndef BKFAC_H
+#define BKFAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL selects the legacy default stream. */
+typedef struct CUstream_st* bkfac_stream_t;
+
+/* ---- precision modes ----------------------------------------------------
+ * BKFAC_F64        U, X, G, S in double; all arithmetic in FP64.
+ * BKFAC_F32        U, X, G, S in float; tall-skinny products in FP32; the
+ *                  CholeskyQR Gram and Cholesky in FP64; core eigensolve in
+ *                  FP32 (FP64 with BKFAC_FLAG_EIG_FP64).
+ * BKFAC_MIXED_BF16 U (master copy), X, G, S in float; the tall-skinny
+ *                  products (U^T X, U M, [U Q] V, G U, U^T G and the apply
+ *                  expansion) take BF16-rounded operands with FP32
+ *                  accumulation; Gram/Cholesky in FP64; periodic FP64
+ *                  re-orthonormalisation (bkfac_reorth) restores U^T U = I. */
+enum { BKFAC_F64 = 0, BKFAC_F32 = 1, BKFAC_MIXED_BF16 = 2 };
+
+/* ---- return / status codes --------------------------------------------- */
+enum {
+  BKFAC_OK = 0,
+  BKFAC_EINVAL = 1,         /* bad argument: sizes, ld, alignment, r > d, n <= 0 */
+  BKFAC_ENOTAPPLICABLE = 2, /* (reserved) a path was requested that the shapes do not allow */
+  BKFAC_ECHOL = 3,          /* CholeskyQR: Gram matrix not positive (all pivots dropped or NaN) */
+  BKFAC_ENOCONV = 4,        /* Jacobi eigensolver hit its sweep cap */
+  BKFAC_ENONFINITE = 5,     /* NaN or Inf met in an input or an intermediate */
+  BKFAC_ETIMEOUT = 6,       /* a bounded device-side wait gave up */
+  BKFAC_ECUDA = 7,          /* a CUDA runtime call failed */
+  BKFAC_EWORKSPACE = 8,     /* workspace pointer NULL, misaligned or too small */
+  BKFAC_ENOMEM = 9          /* host-side allocation failed (batch handles only) */
+};
+
+/* ---- factor flags ------------------------------------------------------- */
+#define BKFAC_FLAG_EIG_FP64 (1u << 0) /* core eigensolve in FP64 also in F32 / MIXED modes */
+
+/* ---- apply flags -------------------------------------------------------- */
+#define BKFAC_SPECTRUM_CONTINUATION (1u << 0) /* Sec. 3.5.1: lam += min sigma, sigma -= min sigma */
+
+/* ---- the low-rank factor state (Sec. 3.1: U~ in R^{d x r}, D~ diagonal) --
+ * All buffers are caller-owned device memory.
+ *   d      factor size (d_in + 1 for the forward factor A, d_out for Gamma)
+ *   r      target rank, 1 <= r <= d
+ *   r_cur  current rank (0 before bkfac_init); maintained by the library on
+ *          the host: after an update r_cur = min(r, r_cur + n) (Brand path) or
+ *          min(r, r_cur + n, d) (dense path).  Modes past the numerical rank
+ *          hold sigma = 0 and may have a zero column in U.
+ *   dtype  BKFAC_F64 (U is double) or BKFAC_F32 / BKFAC_MIXED_BF16 (U float)
+ *   U      device, d x r column-major, leading dimension ldu
+ *   sigma  device, r doubles, eigenvalues in descending order (zero past r_cur)
+ *   step   number of updates applied so far (host counter, incremented by
+ *          bkfac_init / bkfac_update)
+ *   flags  BKFAC_FLAG_* bits
+ * The dense path (explicit d x d factor, Jacobi on its Gram factor) is used
+ * when r + n >= d, where the symmetric Brand update's precondition r + n < d
+ * (Algorithm 3) fails. */
+typedef struct bkfac_factor {
+  int32_t d;
+  int32_t r;
+  int32_t r_cur;
+  int32_t dtype;
+  void* U;
+  int64_t ldu;
+  double* sigma;
+  int64_t step;
+  uint32_t flags;
+  int32_t reserved;
+} bkfac_factor;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int bkfac_version(void);
+
+/* Human-readable text for a code above (static storage, never NULL). */
+const char* bkfac_strerror(int code);
+
+/* Synchronises `stream`, then returns and clears the current device's status
+ * word: BKFAC_OK or the first device-side error code recorded since the last
+ * call.  Returns BKFAC_ECUDA if the synchronisation itself fails. */
+int bkfac_status(bkfac_stream_t stream);
+
+/* ---- workspace sizes ----------------------------------------------------- */
+enum { BKFAC_OP_UPDATE = 0, BKFAC_OP_REORTH = 1 };
+
+/* Bytes of workspace bkfac_init / bkfac_update (op = BKFAC_OP_UPDATE, with
+ * batch width n) or bkfac_reorth (op = BKFAC_OP_REORTH, n ignored) need for
+ * factor f.  Returns 0 for invalid arguments. */
+size_t bkfac_workspace_size(const bkfac_factor* f, int n, int op);
+
+/* Bytes of workspace bkfac_apply needs for the factor pair (fA, fG). */
+size_t bkfac_apply_workspace_size(const bkfac_factor* fA, const bkfac_factor* fG);
+
+/* ---- per-factor calls ---------------------------------------------------- */
+
+/* First state of a factor from its first batch (kappa(0) = 1 in Eq. (5)):
+ * U diag(sigma) U^T <- top-r eigenpairs of X X^T / n, i.e. the update below
+ * from r_cur = 0 with rho = 0.  Sets r_cur = min(r, n) (min(r, n, d) on the
+ * dense path) and step = 1.
+ *   X    device, d x n column-major, leading dimension ldx >= d (the
+ *        factor's dtype: double for F64, float otherwise)
+ *   ws   device workspace of bkfac_workspace_size(f, n, BKFAC_OP_UPDATE) bytes */
+int bkfac_init(bkfac_factor* f, const void* X, int64_t ldx, int n, void* ws, size_t ws_bytes,
+               bkfac_stream_t stream);
+
+/* One B-KFAC update (Algorithm 4 via Algorithm 3, truncation after the
+ * update): with c = (1 - rho)/n,
+ *   M = U^T X;  P = X - U M;  Q R = P (CholeskyQR2, pivots below a relative
+ *   threshold dropped);  M_S = [[rho diag(sigma) + c M M^T, c M R^T],
+ *   [c R M^T, c R R^T]] (Eq. (7) with the substitutions of Sec. 3.1);
+ *   M_S = V diag(lambda) V^T;  U <- [U Q] V[:, :r_new];  sigma <- lambda[:r_new].
+ * The eigensolve runs as one-sided Jacobi on the factor
+ * L = [[diag(sqrt(rho sigma)), sqrt(c) M], [0, sqrt(c) R]] (M_S = L L^T).
+ * U and sigma are overwritten in place; r_cur and step are advanced on the
+ * host.  0 <= rho < 1.  Requires r_cur >= 1 (call bkfac_init first). */
+int bkfac_update(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, void* ws, size_t ws_bytes,
+                 bkfac_stream_t stream);
+
+/* Re-orthonormalisation of U (not in the paper; numerical hygiene for the
+ * mixed-precision path): Q R = U by CholeskyQR in FP64, R diag(sigma) R^T =
+ * W diag(lambda) W^T by Jacobi, U <- Q W, sigma <- lambda.  The represented
+ * matrix U diag(sigma) U^T is unchanged up to rounding. */
+int bkfac_reorth(bkfac_factor* f, void* ws, size_t ws_bytes, bkfac_stream_t stream);
+
+/* Damped inverse application to one layer's gradient (Algorithm 1):
+ *   S = (U_G C_G U_G^T + I/lam_G) G (U_A C_A U_A^T + I/lam_A),
+ *   C = diag(1/(sigma + lam) - 1/lam) over the r_cur stored modes.
+ * Computed in two passes over G:
+ *   pass 1  T1 = G U_A (d_out x r_A), T2 = U_G^T G (r_G x d_in);
+ *   small   T3 = U_G^T T1, W1 = T1 C_A / lam_G + U_G (C_G T3 C_A), W2 = C_G T2 / lam_A;
+ *   pass 2  S = G / (lam_A lam_G) + W1 U_A^T + U_G W2.
+ *   fA, fG  the layer's forward (d = d_in) and backward (d = d_out) factors,
+ *           same dtype, both with r_cur >= 0
+ *   G       device, d_out x d_in row-major, leading dimension ldg >= d_in
+ *   S       device, same layout, lds >= d_in; S == G (in place) is allowed
+ *           when lds == ldg
+ *   lamA, lamG  damping, > 0
+ *   flags   BKFAC_SPECTRUM_CONTINUATION or 0 */
+int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, double lamG, const void* G,
+                int64_t ldg, void* S, int64_t lds, uint32_t flags, void* ws, size_t ws_bytes,
+                bkfac_stream_t stream);
+
+/* Diagnostics for tests: byte offsets, inside an update workspace, of the
+ * intermediates left by the last bkfac_init / bkfac_update that used it:
+ *   out[0] M (r_cur_old x n, column-major, dtype of U)
+ *   out[1] Q (d x n, column-major, ld = out[6]; P before the QR)
+ *   out[2] R (n x n, column-major, double; R = R2 R1)
+ *   out[3] lambda (N = r_cur_old + n doubles, descending, before truncation)
+ *   out[4] N (core size), out[5] leading dimension of M, out[6] ld of Q.
+ * r_cur_old is the factor's r_cur before the update.  Returns BKFAC_EINVAL
+ * for the dense path (which has no M, Q, R). */
+int bkfac_debug_offsets(const bkfac_factor* f, int n, int64_t out[8]);
+
+/* ---- batched calls: all factors of all FC layers -------------------------
+ * A batch groups the two factors of nlayers layers (uneven d, r) with a
+ * common batch width n and dtype.  Each phase of the update and of the apply
+ * runs as one grouped launch over every factor (or every layer); the whole
+ * step can be captured once into a CUDA graph and replayed. */
+typedef struct bkfac_layer_desc {
+  bkfac_factor A;  /* forward factor, d = d_in (+1 for the bias) */
+  bkfac_factor G;  /* backward factor, d = d_out */
+} bkfac_layer_desc;
+
+typedef struct bkfac_batch bkfac_batch;
+
+/* Creates a batch over caller-owned factor buffers (copied descriptors; the
+ * batch advances r_cur / step of its copies).  The handle allocates its own
+ * device workspace and descriptor tables once, here (cudaMalloc), never on
+ * the per-step path.  tune_cache: path of a text file of tuned tile choices
+ * (may be NULL; read if present).  Returns NULL on error. */
+bkfac_batch* bkfac_batch_create(const bkfac_layer_desc* layers, int nlayers, int n, int dtype,
+                                const char* tune_cache);
+
+/* Current descriptor of layer l's factor (which = 0: A, 1: G). */
+int bkfac_batch_get_factor(const bkfac_batch* b, int layer, int which, bkfac_factor* out);
+
+/* Updates every factor: layer l's A factor with X_A[l] (d_A x n, ld ldxA[l]),
+ * its G factor with X_G[l] (d_G x n, ld ldxG[l]).  Factors with r_cur == 0
+ * are initialised instead (rho ignored for them). */
+int bkfac_batch_update(bkfac_batch* b, const void* const* X_A, const int64_t* ldxA, const void* const* X_G,
+                       const int64_t* ldxG, double rho, bkfac_stream_t stream);
+
+/* Applies every layer's damped inverse: S[l] = (G_l-factor)^-1 G[l] (A_l-factor)^-1
+ * with per-layer damping lamA[l], lamG[l] (host arrays). */
+int bkfac_batch_apply(bkfac_batch* b, const void* const* G, const int64_t* ldg, void* const* S,
+                      const int64_t* lds, const double* lamA, const double* lamG, uint32_t flags,
+                      bkfac_stream_t stream);
+
+/* Captures one full step -- bkfac_batch_update(X_A, X_G, rho) followed by
+ * bkfac_batch_apply(G, S, lamA, lamG, flags) with the given pointers -- into
+ * a CUDA graph owned by the batch, then replays it once on `stream`.  Later
+ * calls with capture == 0 replay the graph (same pointers, same rho / lam).
+ * All factors must already be at steady rank (r_cur == r after this step's
+ * update, i.e. no factor still growing), else BKFAC_EINVAL. */
+int bkfac_batch_step_graph(bkfac_batch* b, const void* const* X_A, const int64_t* ldxA, const void* const* X_G,
+                           const int64_t* ldxG, double rho, const void* const* G, const int64_t* ldg,
+                           void* const* S, const int64_t* lds, const double* lamA, const double* lamG,
+                           uint32_t flags, int capture, bkfac_stream_t stream);
+
+void bkfac_batch_destroy(bkfac_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BKFAC_H */

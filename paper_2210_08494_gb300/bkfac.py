@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libbkfac (include/bkfac.h).
+
+Argument marshalling only: every step of the B-KFAC update and apply runs in
+the library's CUDA kernels.  PyTorch provides device memory and streams.  If
+the library is missing or a GPU is absent the calls raise -- there is no CPU
+fallback.
+
+Layout helpers: a d x m column-major matrix with leading dimension ld is a
+torch tensor of shape (m, d) whose row stride is ld (``cols_tensor``); the
+library requires ld * element_size to be a multiple of 16 bytes and a 16-byte
+aligned base.  Gradients are (d_out, d_in) tensors with a padded row stride
+(``grad_tensor``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+F64, F32, MIXED_BF16 = 0, 1, 2
+OK, EINVAL, ENOTAPPLICABLE, ECHOL, ENOCONV, ENONFINITE, ETIMEOUT, ECUDA, EWORKSPACE, ENOMEM = range(10)
+FLAG_EIG_FP64 = 1
+SPECTRUM_CONTINUATION = 1
+OP_UPDATE, OP_REORTH = 0, 1
+
+_TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, MIXED_BF16: torch.float32}
+
+
+class bkfac_factor(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("r", ctypes.c_int32), ("r_cur", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("U", ctypes.c_void_p), ("ldu", ctypes.c_int64), ("sigma", ctypes.c_void_p),
+                ("step", ctypes.c_int64), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+
+
+class bkfac_layer_desc(ctypes.Structure):
+    _fields_ = [("A", bkfac_factor), ("G", bkfac_factor)]
+
+
+class BkfacError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} (code {code})")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libbkfac.so (building it first when missing).  Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise RuntimeError(f"libbkfac not built at {path}")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        P, I, I64, D, S, U32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t, ctypes.c_uint32
+        FP = ctypes.POINTER(bkfac_factor)
+        sig = {
+            "bkfac_version": ([], I),
+            "bkfac_strerror": ([I], ctypes.c_char_p),
+            "bkfac_status": ([P], I),
+            "bkfac_workspace_size": ([FP, I, I], S),
+            "bkfac_apply_workspace_size": ([FP, FP], S),
+            "bkfac_init": ([FP, P, I64, I, P, S, P], I),
+            "bkfac_update": ([FP, P, I64, I, D, P, S, P], I),
+            "bkfac_reorth": ([FP, P, S, P], I),
+            "bkfac_apply": ([FP, FP, D, D, P, I64, P, I64, U32, P, S, P], I),
+            "bkfac_debug_offsets": ([FP, I, ctypes.POINTER(ctypes.c_int64)], I),
+            "bkfac_batch_create": ([ctypes.POINTER(bkfac_layer_desc), I, I, I, ctypes.c_char_p], P),
+            "bkfac_batch_get_factor": ([P, I, I, FP], I),
+            "bkfac_batch_update": ([P, ctypes.POINTER(P), ctypes.POINTER(I64), ctypes.POINTER(P),
+                                    ctypes.POINTER(I64), D, P], I),
+            "bkfac_batch_apply": ([P, ctypes.POINTER(P), ctypes.POINTER(I64), ctypes.POINTER(P),
+                                   ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D), U32, P], I),
+            "bkfac_batch_step_graph": ([P, ctypes.POINTER(P), ctypes.POINTER(I64), ctypes.POINTER(P),
+                                        ctypes.POINTER(I64), D, ctypes.POINTER(P), ctypes.POINTER(I64),
+                                        ctypes.POINTER(P), ctypes.POINTER(I64), ctypes.POINTER(D),
+                                        ctypes.POINTER(D), U32, I, P], I),
+            "bkfac_batch_destroy": ([P], None),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name, None)
+            if fn is None:
+                continue
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    """Names of the bkfac_* functions the loaded library exports (for the ABI tests)."""
+    lib = load()
+    names = []
+    for n in ("bkfac_version", "bkfac_strerror", "bkfac_status", "bkfac_workspace_size",
+              "bkfac_apply_workspace_size", "bkfac_init", "bkfac_update", "bkfac_reorth", "bkfac_apply",
+              "bkfac_debug_offsets", "bkfac_batch_create", "bkfac_batch_get_factor", "bkfac_batch_update",
+              "bkfac_batch_apply", "bkfac_batch_step_graph", "bkfac_batch_destroy"):
+        if hasattr(lib, n):
+            names.append(n)
+    return names
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().bkfac_strerror(int(code)).decode()
+    except Exception:  # library not loadable: still give a readable message
+        return f"error {code}"
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise BkfacError(rc, what)
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _cols_ld(t: torch.Tensor) -> int:
+    """Leading dimension of a (m, d) tensor viewed as a d x m column-major matrix."""
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("expected a 2-D tensor with unit stride along its last dimension")
+    return t.stride(0) if t.shape[0] > 1 else max(t.stride(0), t.shape[1])
+
+
+def padded_ld(d: int, dtype: torch.dtype) -> int:
+    """Smallest leading dimension >= d that keeps rows 16-byte aligned."""
+    per = 16 // torch.tensor([], dtype=dtype).element_size()
+    return (d + per - 1) // per * per
+
+
+def cols_tensor(m: int, d: int, dtype, device="cuda", ld: int | None = None, zero: bool = True) -> torch.Tensor:
+    """A (m, d) view of an (m, ld) buffer: m columns of length d, 16-byte aligned rows."""
+    ld = ld or padded_ld(d, dtype)
+    buf = (torch.zeros if zero else torch.empty)((max(m, 1), ld), dtype=dtype, device=device)
+    return buf[:m, :d]
+
+
+grad_tensor = cols_tensor  # (d_out, d_in) row-major gradient with padded rows
+
+
+def workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    """A 256-byte aligned device byte buffer of at least nbytes."""
+    t = torch.empty(max(int(nbytes), 1) + 256, dtype=torch.uint8, device=device)
+    off = (-t.data_ptr()) % 256
+    return t[off:off + max(int(nbytes), 1)]
+
+
+class Factor:
+    """Device state of one K-factor: U (d x r column-major, stored as an (r, ldu)
+    tensor), sigma (r doubles) and the C descriptor the library updates."""
+
+    def __init__(self, d: int, r: int, dtype: int = F32, device="cuda", flags: int = 0):
+        self.d, self.r, self.dtype = int(d), int(r), int(dtype)
+        tdt = _TORCH_DTYPE[self.dtype]
+        self.U = cols_tensor(self.r, self.d, tdt, device)
+        self.sigma = torch.zeros(self.r, dtype=torch.float64, device=device)
+        self.desc = bkfac_factor(self.d, self.r, 0, self.dtype, self.U.data_ptr(), _cols_ld(self.U),
+                                 self.sigma.data_ptr(), 0, int(flags), 0)
+        self._ws = {}
+
+    @property
+    def r_cur(self) -> int:
+        return int(self.desc.r_cur)
+
+    @property
+    def step(self) -> int:
+        return int(self.desc.step)
+
+    @property
+    def torch_dtype(self):
+        return _TORCH_DTYPE[self.dtype]
+
+    def ws(self, n: int, op: int = OP_UPDATE) -> torch.Tensor:
+        key = (op, n)
+        if key not in self._ws:
+            nb = bkfac_workspace_size(self, n, op)
+            if nb == 0:
+                raise BkfacError(EINVAL, "bkfac_workspace_size")
+            self._ws[key] = workspace(nb, self.U.device)
+        return self._ws[key]
+
+    def state(self):
+        """(U[:, :r_cur] as an (r_cur, d) tensor, sigma[:r_cur])."""
+        k = self.r_cur
+        return self.U[:k], self.sigma[:k]
+
+    def load_state(self, Ut: torch.Tensor, sigma: torch.Tensor, step: int = 1):
+        """Overwrite the state with k = len(sigma) modes (e.g. to resume or to seed a test)."""
+        k = int(sigma.shape[0])
+        self.U.zero_()
+        self.sigma.zero_()
+        self.U[:k].copy_(Ut[:k])
+        self.sigma[:k].copy_(sigma)
+        self.desc.r_cur = k
+        self.desc.step = int(step)
+
+
+# --------------------------------------------------------------------------- C ABI wrappers
+
+
+def bkfac_version() -> int:
+    return int(load().bkfac_version())
+
+
+def bkfac_status(stream=None) -> int:
+    return int(load().bkfac_status(_stream(stream)))
+
+
+def bkfac_workspace_size(f: Factor, n: int, op: int = OP_UPDATE) -> int:
+    return int(load().bkfac_workspace_size(ctypes.byref(f.desc), int(n), int(op)))
+
+
+def bkfac_apply_workspace_size(fA: Factor, fG: Factor) -> int:
+    return int(load().bkfac_apply_workspace_size(ctypes.byref(fA.desc), ctypes.byref(fG.desc)))
+
+
+def bkfac_init(f: Factor, X: torch.Tensor, ws: torch.Tensor | None = None, stream=None):
+    """X: (n, d) tensor view (n columns of length d) of f's dtype on the device."""
+    n = X.shape[0]
+    ws = f.ws(n) if ws is None else ws
+    _check(load().bkfac_init(ctypes.byref(f.desc), _ptr(X), _cols_ld(X), n, _ptr(ws), ws.numel(), _stream(stream)),
+           "bkfac_init")
+
+
+def bkfac_update(f: Factor, X: torch.Tensor, rho: float, ws: torch.Tensor | None = None, stream=None):
+    n = X.shape[0]
+    ws = f.ws(n) if ws is None else ws
+    _check(load().bkfac_update(ctypes.byref(f.desc), _ptr(X), _cols_ld(X), n, float(rho), _ptr(ws), ws.numel(),
+                               _stream(stream)), "bkfac_update")
+
+
+def bkfac_reorth(f: Factor, ws: torch.Tensor | None = None, stream=None):
+    ws = f.ws(0, OP_REORTH) if ws is None else ws
+    _check(load().bkfac_reorth(ctypes.byref(f.desc), _ptr(ws), ws.numel(), _stream(stream)), "bkfac_reorth")
+
+
+def bkfac_apply(fA: Factor, fG: Factor, lamA: float, lamG: float, G: torch.Tensor, S: torch.Tensor,
+                flags: int = 0, ws: torch.Tensor | None = None, stream=None):
+    """G, S: (d_out, d_in) tensors with unit column stride (S may be G)."""
+    if ws is None:
+        key = ("apply", id(fG))
+        if key not in fA._ws:
+            fA._ws[key] = workspace(bkfac_apply_workspace_size(fA, fG), fA.U.device)
+        ws = fA._ws[key]
+    _check(load().bkfac_apply(ctypes.byref(fA.desc), ctypes.byref(fG.desc), float(lamA), float(lamG), _ptr(G),
+                              G.stride(0), _ptr(S), S.stride(0), int(flags), _ptr(ws), ws.numel(), _stream(stream)),
+           "bkfac_apply")
+
+
+def bkfac_debug_offsets(f: Factor, n: int):
+    out = (ctypes.c_int64 * 8)()
+    _check(load().bkfac_debug_offsets(ctypes.byref(f.desc), int(n), out), "bkfac_debug_offsets")
+    return list(out)

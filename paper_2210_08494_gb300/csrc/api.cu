@@ -1,0 +1,782 @@
+// api.cu -- the C ABI of libbkfac: argument validation, workspace layout and
+// the launch sequence of each call (see include/bkfac.h).
+//
+// Update (Algorithm 4 via Algorithm 3), Brand path, per factor:
+//   scale = max_j ||x_j||^2                                (pivot reference)
+//   M = U^T X                       split-K GEMM           (Algorithm 3, first step)
+//   P = X - U M                     GEMM + epilogue
+//   G1 = P^T P (FP64), R1 = chol(G1), Q1 = P R1^-1          CholeskyQR2, pass 1
+//   G2 = Q1^T Q1 (FP64), R2 = chol(G2), Q = Q1 R2^-1        pass 2;  R = R2 R1
+//   L = [[diag(sqrt(rho sigma)), sqrt(c) M], [0, sqrt(c) R]]   (M_S = L L^T, Eq. (7))
+//   one-sided Jacobi on L -> lambda, V (sorted, truncated to r)
+//   U <- [U Q] V[:, :r_new], sigma <- lambda[:r_new]
+// Dense path (r + n >= d): Jacobi on F = [U sqrt(rho sigma), sqrt(c) X].
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace bkfac {
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxSweeps = 40;
+
+size_t es_of(DType t) { return t == DT_F64 ? 8 : 4; }
+DType dt_of(int dtype) { return dtype == BKFAC_F64 ? DT_F64 : DT_F32; }
+
+struct Layout {
+  size_t total = 0;
+  size_t add(size_t bytes) {
+    const size_t off = total;
+    total += (size_t)round_up((int64_t)std::max<size_t>(bytes, 1), kAlign);
+    return off;
+  }
+};
+
+bool valid_factor(const bkfac_factor* f) {
+  if (!f || f->d < 1 || f->r < 1 || f->r > f->d || f->r_cur < 0 || f->r_cur > f->r) return false;
+  if (f->dtype != BKFAC_F64 && f->dtype != BKFAC_F32 && f->dtype != BKFAC_MIXED_BF16) return false;
+  if (!f->U || !f->sigma || f->ldu < f->d) return false;
+  const size_t es = f->dtype == BKFAC_F64 ? 8 : 4;
+  if (((uintptr_t)f->U) % 16 != 0 || (f->ldu * (int64_t)es) % 16 != 0) return false;
+  if (((uintptr_t)f->sigma) % 8 != 0) return false;
+  return true;
+}
+
+bool dense_path(const bkfac_factor* f, int n) { return (int64_t)f->r + n >= f->d; }
+
+// element type of U / X, Jacobi type, GEMM accumulator
+struct Prec {
+  DType t, jt, acc;
+  bool bf16;
+  double u_t;  // unit roundoff governing the residual threshold
+};
+Prec prec_of(const bkfac_factor* f) {
+  Prec p;
+  p.t = dt_of(f->dtype);
+  p.acc = p.t;
+  p.bf16 = f->dtype == BKFAC_MIXED_BF16;
+  p.jt = (f->dtype == BKFAC_F64 || (f->flags & BKFAC_FLAG_EIG_FP64)) ? DT_F64 : DT_F32;
+  p.u_t = f->dtype == BKFAC_F64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+  return p;
+}
+
+double jacobi_tol(int rows, DType jt) {
+  const double u = jt == DT_F64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+  return std::max(4.0 * std::sqrt((double)std::max(rows, 1)), 32.0) * u;
+}
+
+int64_t ld_of(int d) { return round_up(d, 32); }
+
+// ------------------------------------------------------------------ update workspace plan
+struct UpdatePlan {
+  bool dense;
+  int d, r, k, n, N, r_new;
+  Prec pr;
+  int64_t ldq, ldm, ldv;
+  int C, b, rows_pad, cols_pad;  // Jacobi plan of this call
+  int rows_cap, cols_cap;        // capacity of L
+  size_t o_scale, o_M, o_part, o_P, o_Q1, o_Q, o_G, o_R1, o_R2, o_Rinv, o_L, o_cn, o_lam, o_V, o_Un, o_sw;
+  size_t total;
+};
+
+// split-K scratch for any product up to M x N (fewer output tiles may use more
+// splits, never more than 32)
+size_t partial_bytes(int M, int N, int K, size_t acc_es) {
+  (void)K;
+  return (size_t)32 * std::max(M, 1) * std::max(N, 1) * acc_es;
+}
+
+UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
+  UpdatePlan p{};
+  p.pr = prec_of(f);
+  p.d = f->d;
+  p.r = f->r;
+  p.k = k;
+  p.n = n;
+  p.dense = dense_path(f, n);
+  p.ldq = ld_of(f->d);
+  const size_t es = es_of(p.pr.t), jes = es_of(p.pr.jt), aes = es_of(p.pr.acc);
+  Layout L;
+  int rows_cap, cols_cap;
+  if (p.dense) {
+    p.N = k + n;
+    p.r_new = std::min(std::min(f->r, k + n), f->d);
+    jacobi_plan(f->d, k + n, p.pr.jt, &p.C, &p.b, &p.rows_pad, &p.cols_pad);
+    int C2, b2, rp2, cp2;
+    jacobi_plan(f->d, f->r + n, p.pr.jt, &C2, &b2, &rp2, &cp2);
+    rows_cap = rp2;
+    cols_cap = (int)round_up(f->r + n, 32) + 64;
+    p.o_L = L.add((size_t)rows_cap * cols_cap * jes);
+    p.o_cn = L.add((size_t)cols_cap * 8);
+    p.o_lam = L.add((size_t)cols_cap * 8);
+    p.o_sw = L.add(16);
+  } else {
+    const int kmax = f->r, Nmax = f->r + n;
+    p.N = k + n;
+    p.r_new = std::min(f->r, k + n);
+    p.ldm = std::max(kmax, 1);
+    p.ldv = round_up(Nmax, 4);
+    jacobi_plan(p.N, p.N, p.pr.jt, &p.C, &p.b, &p.rows_pad, &p.cols_pad);
+    int C2, b2, rp2, cp2;
+    jacobi_plan(Nmax, Nmax, p.pr.jt, &C2, &b2, &rp2, &cp2);
+    rows_cap = rp2;
+    cols_cap = (int)round_up(Nmax, 32) + 64;
+    p.o_scale = L.add(8);
+    p.o_M = L.add((size_t)p.ldm * n * es);
+    const size_t part = std::max(partial_bytes(kmax, n, f->d, aes), partial_bytes(n, n, f->d, 8));
+    p.o_part = L.add(part);
+    p.o_P = L.add((size_t)p.ldq * n * es);
+    p.o_Q1 = L.add((size_t)p.ldq * n * es);
+    p.o_Q = L.add((size_t)p.ldq * n * es);
+    p.o_G = L.add((size_t)n * n * 8);
+    p.o_R1 = L.add((size_t)n * n * 8);
+    p.o_R2 = L.add((size_t)n * n * 8);
+    p.o_Rinv = L.add((size_t)n * n * es);
+    p.o_L = L.add((size_t)rows_cap * cols_cap * jes);
+    p.o_cn = L.add((size_t)cols_cap * 8);
+    p.o_lam = L.add((size_t)cols_cap * 8);
+    p.o_V = L.add((size_t)p.ldv * f->r * es);
+    p.o_Un = L.add((size_t)p.ldq * f->r * es);
+    p.o_sw = L.add(16);
+  }
+  p.rows_cap = rows_cap;
+  p.cols_cap = cols_cap;
+  p.total = L.total;
+  return p;
+}
+
+// ------------------------------------------------------------------ reorth plan
+struct ReorthPlan {
+  int d, k;
+  Prec pr;
+  int64_t ldq, ldv;
+  int C, b, rows_pad, cols_pad, rows_cap, cols_cap;
+  size_t o_part, o_G, o_R, o_Rinv, o_Q, o_L, o_cn, o_lam, o_V, o_Un, o_sw, total;
+};
+
+ReorthPlan plan_reorth(const bkfac_factor* f, int k) {
+  ReorthPlan p{};
+  p.pr = prec_of(f);
+  p.d = f->d;
+  p.k = k;
+  p.ldq = ld_of(f->d);
+  const int kmax = f->r;
+  p.ldv = round_up(std::max(kmax, 1), 4);
+  const size_t es = es_of(p.pr.t), jes = es_of(p.pr.jt);
+  jacobi_plan(std::max(k, 1), std::max(k, 1), p.pr.jt, &p.C, &p.b, &p.rows_pad, &p.cols_pad);
+  int C2, b2, rp2, cp2;
+  jacobi_plan(kmax, kmax, p.pr.jt, &C2, &b2, &rp2, &cp2);
+  p.rows_cap = rp2;
+  p.cols_cap = (int)round_up(kmax, 32) + 64;
+  Layout L;
+  p.o_part = L.add(partial_bytes(kmax, kmax, f->d, 8));
+  p.o_G = L.add((size_t)kmax * kmax * 8);
+  p.o_R = L.add((size_t)kmax * kmax * 8);
+  p.o_Rinv = L.add((size_t)kmax * kmax * es);
+  p.o_Q = L.add((size_t)p.ldq * kmax * es);
+  p.o_L = L.add((size_t)p.rows_cap * p.cols_cap * jes);
+  p.o_cn = L.add((size_t)p.cols_cap * 8);
+  p.o_lam = L.add((size_t)p.cols_cap * 8);
+  p.o_V = L.add((size_t)p.ldv * kmax * es);
+  p.o_Un = L.add((size_t)p.ldq * kmax * es);
+  p.o_sw = L.add(16);
+  p.total = L.total;
+  return p;
+}
+
+// ------------------------------------------------------------------ apply plan
+struct ApplyPlan {
+  int dA, dG, kA, kG;
+  Prec pr;
+  int64_t ld1, ld2, ldw;
+  size_t o_T1, o_T2, o_T3, o_W1, o_part, o_cA, o_cG, o_cAo, o_cGo, o_alpha, total;
+};
+
+ApplyPlan plan_apply(const bkfac_factor* fA, const bkfac_factor* fG, int kA, int kG) {
+  ApplyPlan p{};
+  p.pr = prec_of(fA);
+  p.dA = fA->d;
+  p.dG = fG->d;
+  p.kA = kA;
+  p.kG = kG;
+  const int rA = fA->r, rG = fG->r;
+  p.ld1 = ld_of(p.dG);  // T1, W1: d_out x r_A column-major
+  p.ld2 = ld_of(p.dA);  // T2: r_G x d_in row-major
+  p.ldw = std::max(rG, 1);
+  const size_t es = es_of(p.pr.t), aes = es_of(p.pr.acc);
+  Layout L;
+  p.o_T1 = L.add((size_t)p.ld1 * rA * es);
+  p.o_W1 = L.add((size_t)p.ld1 * rA * es);
+  p.o_T2 = L.add((size_t)p.ld2 * rG * es);
+  p.o_T3 = L.add((size_t)p.ldw * rA * es);
+  p.o_part = L.add(partial_bytes(rG, rA, p.dG, aes));
+  p.o_cA = L.add((size_t)rA * 8);
+  p.o_cG = L.add((size_t)rG * 8);
+  p.o_cAo = L.add((size_t)rA * 8);
+  p.o_cGo = L.add((size_t)rG * 8);
+  p.o_alpha = L.add(8);
+  p.total = L.total;
+  return p;
+}
+
+template <typename P>
+P* at(void* ws, size_t off) {
+  return (P*)((char*)ws + off);
+}
+
+int cuda_rc(int e) { return e == 0 ? BKFAC_OK : BKFAC_ECUDA; }
+
+#define BK_TRY(expr)                     \
+  do {                                   \
+    int _e = (expr);                     \
+    if (_e != 0) return BKFAC_ECUDA;     \
+  } while (0)
+
+GemmArgs gemm_base() {
+  GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.alpha = 1.0;
+  g.beta = 0.0;
+  g.splits = 1;
+  return g;
+}
+
+// Gram G = A^T A of a d x n column-major matrix (FP64 accumulation), output n x n
+int run_gram(const void* A, int64_t lda, int d, int n, Prec pr, double* G, void* part, cudaStream_t s) {
+  GemmArgs g = gemm_base();
+  g.M = n;
+  g.N = n;
+  g.K0 = d;
+  g.A0 = A;
+  g.lda0 = lda;
+  g.B0 = A;
+  g.ldb0 = lda;
+  g.a_kmaj = true;
+  g.b_kmaj = true;
+  g.C = G;
+  g.ldc = n;
+  g.splits = gemm_pick_splits(n, n, d, 152);
+  g.partial = part;
+  return gemm_run(g, pr.t, DT_F64, DT_F64, s);
+}
+
+// Q = P Rinv (d x n times n x n upper), output column-major ld ldq
+int run_trmm(const void* P, int64_t ldp, int d, int n, const void* Rinv, Prec pr, void* Q, int64_t ldq,
+             cudaStream_t s) {
+  GemmArgs g = gemm_base();
+  g.M = d;
+  g.N = n;
+  g.K0 = n;
+  g.A0 = P;
+  g.lda0 = ldp;
+  g.a_kmaj = false;
+  g.B0 = Rinv;
+  g.ldb0 = n;
+  g.b_kmaj = true;
+  g.C = Q;
+  g.ldc = ldq;
+  return gemm_run(g, pr.t, pr.acc, pr.t, s);
+}
+
+// the full update sequence for one factor (k = current rank, rho, c already set)
+int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, void* ws,
+                   const UpdatePlan& p, cudaStream_t s) {
+  const Prec& pr = p.pr;
+  const int d = f->d, k = p.k;
+  const double c = (1.0 - rho) / (double)n;
+  if (p.dense) {
+    DenseArgs a;
+    a.d = d;
+    a.k = k;
+    a.n = n;
+    a.rows_pad = p.rows_pad;
+    a.cols_pad = p.cols_pad;
+    a.rho = rho;
+    a.c = c;
+    a.U = f->U;
+    a.ldu = f->ldu;
+    a.sigma = f->sigma;
+    a.X = X;
+    a.ldx = ldx;
+    a.F = at<void>(ws, p.o_L);
+    a.colnorm2 = at<double>(ws, p.o_cn);
+    BK_TRY(launch_assemble_dense(a, pr.t, pr.jt, s));
+    JacobiProblem jp;
+    jp.W = a.F;
+    jp.rows = d;
+    jp.rows_pad = p.rows_pad;
+    jp.cols_pad = p.cols_pad;
+    jp.b = p.b;
+    jp.colnorm2 = a.colnorm2;
+    jp.sweeps_out = at<int>(ws, p.o_sw);
+    BK_TRY(launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(d, pr.jt), kMaxSweeps, s));
+    SortArgs so;
+    so.W = a.F;
+    so.rows = d;
+    so.rows_pad = p.rows_pad;
+    so.cols = k + n;
+    so.r_out = p.r_new;
+    so.V = f->U;
+    so.ldv = f->ldu;
+    so.sig = f->sigma;
+    so.r_sig = f->r;
+    so.lam_sorted = at<double>(ws, p.o_lam);
+    so.colnorm2 = a.colnorm2;
+    so.cols_pad = p.cols_pad;
+    BK_TRY(launch_sort_output(so, pr.jt, pr.t, s));
+    // columns past r_new are cleared so U holds no stale modes
+    if (p.r_new < f->r) {
+      BK_TRY(launch_finalize(f->U, f->ldu, f->U, f->ldu, d, p.r_new, f->r, pr.t, s));
+    }
+    return BKFAC_OK;
+  }
+
+  double* scale = at<double>(ws, p.o_scale);
+  void* M = at<void>(ws, p.o_M);
+  void* part = at<void>(ws, p.o_part);
+  void* P = at<void>(ws, p.o_P);
+  void* Q1 = at<void>(ws, p.o_Q1);
+  void* Q = at<void>(ws, p.o_Q);
+  double* Gm = at<double>(ws, p.o_G);
+  double* R1 = at<double>(ws, p.o_R1);
+  double* R2 = at<double>(ws, p.o_R2);
+  void* Rinv = at<void>(ws, p.o_Rinv);
+  BK_TRY(launch_colnorm_max(X, ldx, d, n, pr.t, scale, s));
+
+  const void* Pp = X;
+  int64_t ldp = ldx;
+  if (k > 0) {
+    // M = U^T X  (k x n, K = d)
+    GemmArgs g = gemm_base();
+    g.M = k;
+    g.N = n;
+    g.K0 = d;
+    g.A0 = f->U;
+    g.lda0 = f->ldu;
+    g.a_kmaj = true;
+    g.B0 = X;
+    g.ldb0 = ldx;
+    g.b_kmaj = true;
+    g.round_bf16 = pr.bf16;
+    g.C = M;
+    g.ldc = p.ldm;
+    g.splits = gemm_pick_splits(k, n, d, 152);
+    g.partial = part;
+    BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+    // P = X - U M  (d x n, K = k)
+    GemmArgs h = gemm_base();
+    h.M = d;
+    h.N = n;
+    h.K0 = k;
+    h.A0 = f->U;
+    h.lda0 = f->ldu;
+    h.a_kmaj = false;
+    h.B0 = M;
+    h.ldb0 = p.ldm;
+    h.b_kmaj = true;
+    h.round_bf16 = pr.bf16;
+    h.C = P;
+    h.ldc = p.ldq;
+    h.D = X;
+    h.ldd = ldx;
+    h.alpha = -1.0;
+    h.beta = 1.0;
+    BK_TRY(gemm_run(h, pr.t, pr.acc, pr.t, s));
+    Pp = P;
+    ldp = p.ldq;
+  }
+  // CholeskyQR2 with FP64 Gram and Cholesky
+  const double ue = pr.bf16 ? 3.90625e-3 : pr.u_t;
+  const double thr1 = pr.bf16 ? (2.0 * ue) * (2.0 * ue) : (64.0 * ue) * (64.0 * ue);
+  const double thr2 = (64.0 * pr.u_t) * (64.0 * pr.u_t);
+  BK_TRY(run_gram(Pp, ldp, d, n, pr, Gm, part, s));
+  BK_TRY(launch_chol(Gm, n, R1, thr1, scale, s));
+  BK_TRY(launch_trinv(R1, n, Rinv, pr.t, s));
+  BK_TRY(run_trmm(Pp, ldp, d, n, Rinv, pr, Q1, p.ldq, s));
+  BK_TRY(run_gram(Q1, p.ldq, d, n, pr, Gm, part, s));
+  BK_TRY(launch_chol(Gm, n, R2, thr2, nullptr, s));
+  BK_TRY(launch_trinv(R2, n, Rinv, pr.t, s));
+  BK_TRY(run_trmm(Q1, p.ldq, d, n, Rinv, pr, Q, p.ldq, s));
+  // core factor L and its Jacobi eigensolve
+  CoreArgs ca;
+  ca.k = k;
+  ca.n = n;
+  ca.N = k + n;
+  ca.rows_pad = p.rows_pad;
+  ca.cols_pad = p.cols_pad;
+  ca.rho = rho;
+  ca.c = c;
+  ca.sigma = f->sigma;
+  ca.M = M;
+  ca.ldm = p.ldm;
+  ca.R1 = R1;
+  ca.R2 = R2;
+  ca.L = at<void>(ws, p.o_L);
+  ca.colnorm2 = at<double>(ws, p.o_cn);
+  BK_TRY(launch_assemble_core(ca, pr.t, pr.jt, s));
+  JacobiProblem jp;
+  jp.W = ca.L;
+  jp.rows = p.N;
+  jp.rows_pad = p.rows_pad;
+  jp.cols_pad = p.cols_pad;
+  jp.b = p.b;
+  jp.colnorm2 = ca.colnorm2;
+  jp.sweeps_out = at<int>(ws, p.o_sw);
+  BK_TRY(launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(p.N, pr.jt), kMaxSweeps, s));
+  SortArgs so;
+  so.W = ca.L;
+  so.rows = p.N;
+  so.rows_pad = p.rows_pad;
+  so.cols = p.N;
+  so.r_out = p.r_new;
+  so.V = at<void>(ws, p.o_V);
+  so.ldv = p.ldv;
+  so.sig = f->sigma;
+  so.r_sig = f->r;
+  so.lam_sorted = at<double>(ws, p.o_lam);
+  so.colnorm2 = ca.colnorm2;
+  so.cols_pad = p.cols_pad;
+  // sigma is only read by the core assembly above, so it can be overwritten here
+  BK_TRY(launch_sort_output(so, pr.jt, pr.t, s));
+  // U' = [U Q] V[:, :r_new]
+  GemmArgs g = gemm_base();
+  g.M = d;
+  g.N = p.r_new;
+  g.K0 = k;
+  g.K1 = n;
+  g.A0 = f->U;
+  g.lda0 = f->ldu;
+  g.A1 = Q;
+  g.lda1 = p.ldq;
+  g.a_kmaj = false;
+  g.B0 = so.V;
+  g.ldb0 = p.ldv;
+  g.B1 = (const char*)so.V + (size_t)k * es_of(pr.t);
+  g.ldb1 = p.ldv;
+  g.b_kmaj = true;
+  g.round_bf16 = pr.bf16;
+  g.C = at<void>(ws, p.o_Un);
+  g.ldc = p.ldq;
+  BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+  BK_TRY(launch_finalize(f->U, f->ldu, g.C, p.ldq, d, p.r_new, f->r, pr.t, s));
+  return BKFAC_OK;
+}
+
+int check_ws(void* ws, size_t ws_bytes, size_t need) {
+  if (need == 0) return BKFAC_OK;
+  if (!ws || ((uintptr_t)ws) % kAlign != 0 || ws_bytes < need) return BKFAC_EWORKSPACE;
+  return BKFAC_OK;
+}
+
+bool jacobi_fits(int C, int b, int rows_pad, DType jt) {
+  (void)C;
+  return jacobi_smem_bytes(b, rows_pad, jt) <= 227 * 1024;
+}
+
+int update_common(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, void* ws, size_t ws_bytes,
+                  cudaStream_t s, bool init) {
+  if (!valid_factor(f) || !X || n < 1 || ldx < f->d) return BKFAC_EINVAL;
+  const size_t es = f->dtype == BKFAC_F64 ? 8 : 4;
+  if (((uintptr_t)X) % 16 != 0 || (ldx * (int64_t)es) % 16 != 0) return BKFAC_EINVAL;
+  if (!(rho >= 0.0 && rho < 1.0)) return BKFAC_EINVAL;
+  if (!init && f->r_cur < 1) return BKFAC_EINVAL;
+  const int k = init ? 0 : f->r_cur;
+  const UpdatePlan cap = plan_update(f, n, f->r);
+  UpdatePlan p = plan_update(f, n, k);
+  p.total = cap.total;
+  if (p.rows_pad > p.rows_cap || p.cols_pad > p.cols_cap) return BKFAC_EINVAL;
+  if (!jacobi_fits(p.C, p.b, p.rows_pad, p.pr.jt)) return BKFAC_EINVAL;
+  if (p.N > 8192 || (!p.dense && n > 1024)) return BKFAC_EINVAL;
+  int rc = check_ws(ws, ws_bytes, cap.total);
+  if (rc) return rc;
+  rc = enqueue_update(f, X, ldx, n, init ? 0.0 : rho, ws, p, s);
+  if (rc) return rc;
+  f->r_cur = p.r_new;
+  f->step = init ? 1 : f->step + 1;
+  return BKFAC_OK;
+}
+
+}  // namespace
+}  // namespace bkfac
+
+using namespace bkfac;
+
+extern "C" {
+
+int bkfac_version(void) { return 100; }
+
+const char* bkfac_strerror(int code) {
+  switch (code) {
+    case BKFAC_OK: return "ok";
+    case BKFAC_EINVAL: return "invalid argument";
+    case BKFAC_ENOTAPPLICABLE: return "path not applicable to these shapes";
+    case BKFAC_ECHOL: return "CholeskyQR breakdown";
+    case BKFAC_ENOCONV: return "Jacobi eigensolver did not converge within its sweep cap";
+    case BKFAC_ENONFINITE: return "non-finite value in an input or intermediate";
+    case BKFAC_ETIMEOUT: return "bounded device wait timed out";
+    case BKFAC_ECUDA: return "CUDA runtime error";
+    case BKFAC_EWORKSPACE: return "workspace missing, misaligned or too small";
+    case BKFAC_ENOMEM: return "host allocation failed";
+    default: return "unknown error code";
+  }
+}
+
+int bkfac_status(bkfac_stream_t stream) {
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return BKFAC_ECUDA;
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, bkfac::g_status, sizeof(int)) != cudaSuccess) return BKFAC_ECUDA;
+  const int zero = 0;
+  if (cudaMemcpyToSymbol(bkfac::g_status, &zero, sizeof(int)) != cudaSuccess) return BKFAC_ECUDA;
+  return v;
+}
+
+size_t bkfac_workspace_size(const bkfac_factor* f, int n, int op) {
+  if (!valid_factor(f)) return 0;
+  if (op == BKFAC_OP_UPDATE) {
+    if (n < 1) return 0;
+    return plan_update(f, n, f->r).total;
+  }
+  if (op == BKFAC_OP_REORTH) return plan_reorth(f, f->r).total;
+  return 0;
+}
+
+size_t bkfac_apply_workspace_size(const bkfac_factor* fA, const bkfac_factor* fG) {
+  if (!valid_factor(fA) || !valid_factor(fG) || fA->dtype != fG->dtype) return 0;
+  return plan_apply(fA, fG, fA->r, fG->r).total;
+}
+
+int bkfac_init(bkfac_factor* f, const void* X, int64_t ldx, int n, void* ws, size_t ws_bytes,
+               bkfac_stream_t stream) {
+  return update_common(f, X, ldx, n, 0.0, ws, ws_bytes, (cudaStream_t)stream, true);
+}
+
+int bkfac_update(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, void* ws, size_t ws_bytes,
+                 bkfac_stream_t stream) {
+  return update_common(f, X, ldx, n, rho, ws, ws_bytes, (cudaStream_t)stream, false);
+}
+
+int bkfac_reorth(bkfac_factor* f, void* ws, size_t ws_bytes, bkfac_stream_t stream) {
+  if (!valid_factor(f)) return BKFAC_EINVAL;
+  const int k = f->r_cur;
+  if (k == 0) return BKFAC_OK;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const ReorthPlan cap = plan_reorth(f, f->r);
+  const ReorthPlan p = plan_reorth(f, k);
+  int rc = check_ws(ws, ws_bytes, cap.total);
+  if (rc) return rc;
+  if (p.rows_pad > cap.rows_cap || p.cols_pad > cap.cols_cap) return BKFAC_EINVAL;
+  if (!jacobi_fits(p.C, p.b, p.rows_pad, p.pr.jt)) return BKFAC_EINVAL;
+  const Prec& pr = p.pr;
+  const int d = f->d;
+  double* Gm = at<double>(ws, cap.o_G);
+  double* R = at<double>(ws, cap.o_R);
+  void* Rinv = at<void>(ws, cap.o_Rinv);
+  void* Q = at<void>(ws, cap.o_Q);
+  BK_TRY(run_gram(f->U, f->ldu, d, k, pr, Gm, at<void>(ws, cap.o_part), s));
+  BK_TRY(launch_chol(Gm, k, R, (64.0 * pr.u_t) * (64.0 * pr.u_t), nullptr, s));
+  BK_TRY(launch_trinv(R, k, Rinv, pr.t, s));
+  BK_TRY(run_trmm(f->U, f->ldu, d, k, Rinv, pr, Q, cap.ldq, s));
+  void* Lm = at<void>(ws, cap.o_L);
+  double* cn = at<double>(ws, cap.o_cn);
+  BK_TRY(launch_assemble_reorth(R, f->sigma, k, p.rows_pad, p.cols_pad, Lm, cn, pr.jt, s));
+  JacobiProblem jp;
+  jp.W = Lm;
+  jp.rows = k;
+  jp.rows_pad = p.rows_pad;
+  jp.cols_pad = p.cols_pad;
+  jp.b = p.b;
+  jp.colnorm2 = cn;
+  jp.sweeps_out = at<int>(ws, cap.o_sw);
+  BK_TRY(launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(k, pr.jt), kMaxSweeps, s));
+  SortArgs so;
+  so.W = Lm;
+  so.rows = k;
+  so.rows_pad = p.rows_pad;
+  so.cols = k;
+  so.r_out = k;
+  so.V = at<void>(ws, cap.o_V);
+  so.ldv = cap.ldv;
+  so.sig = f->sigma;
+  so.r_sig = f->r;
+  so.lam_sorted = at<double>(ws, cap.o_lam);
+  so.colnorm2 = cn;
+  so.cols_pad = p.cols_pad;
+  BK_TRY(launch_sort_output(so, pr.jt, pr.t, s));
+  GemmArgs g = gemm_base();
+  g.M = d;
+  g.N = k;
+  g.K0 = k;
+  g.A0 = Q;
+  g.lda0 = cap.ldq;
+  g.a_kmaj = false;
+  g.B0 = so.V;
+  g.ldb0 = cap.ldv;
+  g.b_kmaj = true;
+  g.C = at<void>(ws, cap.o_Un);
+  g.ldc = cap.ldq;
+  BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+  BK_TRY(launch_finalize(f->U, f->ldu, g.C, cap.ldq, d, k, f->r, pr.t, s));
+  return BKFAC_OK;
+}
+
+int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, double lamG, const void* G,
+                int64_t ldg, void* S, int64_t lds, uint32_t flags, void* ws, size_t ws_bytes,
+                bkfac_stream_t stream) {
+  if (!valid_factor(fA) || !valid_factor(fG) || fA->dtype != fG->dtype) return BKFAC_EINVAL;
+  if (!G || !S || ldg < fA->d || lds < fA->d) return BKFAC_EINVAL;
+  if (!(lamA > 0.0) || !(lamG > 0.0) || !std::isfinite(lamA) || !std::isfinite(lamG)) return BKFAC_EINVAL;
+  if ((flags & ~(uint32_t)BKFAC_SPECTRUM_CONTINUATION) != 0) return BKFAC_EINVAL;
+  if (S == G && lds != ldg) return BKFAC_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int kA = fA->r_cur, kG = fG->r_cur;
+  const ApplyPlan cap = plan_apply(fA, fG, fA->r, fG->r);
+  const ApplyPlan p = plan_apply(fA, fG, kA, kG);
+  int rc = check_ws(ws, ws_bytes, cap.total);
+  if (rc) return rc;
+  const Prec& pr = p.pr;
+  const int dA = fA->d, dG = fG->d;
+  void* T1 = at<void>(ws, cap.o_T1);
+  void* W1 = at<void>(ws, cap.o_W1);
+  void* T2 = at<void>(ws, cap.o_T2);
+  void* T3 = at<void>(ws, cap.o_T3);
+  double* cA = at<double>(ws, cap.o_cA);
+  double* cG = at<double>(ws, cap.o_cG);
+  double* cAo = at<double>(ws, cap.o_cAo);
+  double* cGo = at<double>(ws, cap.o_cGo);
+  double* alpha = at<double>(ws, cap.o_alpha);
+  ApplyCoefArgs ca;
+  ca.sigA = fA->sigma;
+  ca.kA = kA;
+  ca.sigG = fG->sigma;
+  ca.kG = kG;
+  ca.lamA = lamA;
+  ca.lamG = lamG;
+  ca.continuation = (flags & BKFAC_SPECTRUM_CONTINUATION) ? 1 : 0;
+  ca.cA = cA;
+  ca.cG = cG;
+  ca.cA_over = cAo;
+  ca.cG_over = cGo;
+  ca.alpha = alpha;
+  BK_TRY(launch_apply_coefs(ca, s));
+  // pass 1: T1 = G U_A (d_out x kA), T2 = diag(C_G / lamA') U_G^T G (kG x d_in, row-major)
+  if (kA > 0) {
+    GemmArgs g = gemm_base();
+    g.M = dG;
+    g.N = kA;
+    g.K0 = dA;
+    g.A0 = G;
+    g.lda0 = ldg;
+    g.a_kmaj = true;
+    g.B0 = fA->U;
+    g.ldb0 = fA->ldu;
+    g.b_kmaj = true;
+    g.round_bf16 = pr.bf16;
+    g.C = T1;
+    g.ldc = cap.ld1;
+    BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+  }
+  if (kG > 0) {
+    GemmArgs g = gemm_base();
+    g.M = dA;
+    g.N = kG;
+    g.K0 = dG;
+    g.A0 = G;
+    g.lda0 = ldg;
+    g.a_kmaj = false;
+    g.B0 = fG->U;
+    g.ldb0 = fG->ldu;
+    g.b_kmaj = true;
+    g.round_bf16 = pr.bf16;
+    g.C = T2;  // column-major d_in x kG == row-major kG x d_in
+    g.ldc = cap.ld2;
+    g.cs = cGo;
+    BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+  }
+  // small: T3' = diag(C_G) (U_G^T T1) diag(C_A);  W1 = T1 diag(C_A / lamG') + U_G T3'
+  if (kA > 0) {
+    if (kG > 0) {
+      GemmArgs g = gemm_base();
+      g.M = kG;
+      g.N = kA;
+      g.K0 = dG;
+      g.A0 = fG->U;
+      g.lda0 = fG->ldu;
+      g.a_kmaj = true;
+      g.B0 = T1;
+      g.ldb0 = cap.ld1;
+      g.b_kmaj = true;
+      g.C = T3;
+      g.ldc = cap.ldw;
+      g.rs = cG;
+      g.cs = cA;
+      g.splits = gemm_pick_splits(kG, kA, dG, 152);
+      g.partial = at<void>(ws, cap.o_part);
+      BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+    }
+    GemmArgs g = gemm_base();
+    g.M = dG;
+    g.N = kA;
+    g.K0 = kG;
+    g.A0 = fG->U;
+    g.lda0 = fG->ldu;
+    g.a_kmaj = false;
+    g.B0 = T3;
+    g.ldb0 = cap.ldw;
+    g.b_kmaj = true;
+    g.C = W1;
+    g.ldc = cap.ld1;
+    g.D = T1;
+    g.ldd = cap.ld1;
+    g.beta = 1.0;
+    g.ds = cAo;
+    BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+  }
+  // pass 2: S = alpha G + W1 U_A^T + U_G W2
+  {
+    GemmArgs g = gemm_base();
+    g.M = dG;
+    g.N = dA;
+    g.K0 = kA;
+    g.K1 = kG;
+    g.A0 = W1;
+    g.lda0 = cap.ld1;
+    g.A1 = fG->U;
+    g.lda1 = fG->ldu;
+    g.a_kmaj = false;
+    g.B0 = fA->U;
+    g.ldb0 = fA->ldu;
+    g.B1 = T2;
+    g.ldb1 = cap.ld2;
+    g.b_kmaj = false;
+    g.round_bf16 = pr.bf16;
+    g.C = S;
+    g.ldc = lds;
+    g.c_rowmaj = true;
+    g.D = G;
+    g.ldd = ldg;
+    g.beta_dev = alpha;
+    g.beta = 1.0;
+    BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+  }
+  return BKFAC_OK;
+}
+
+int bkfac_debug_offsets(const bkfac_factor* f, int n, int64_t out[8]) {
+  if (!valid_factor(f) || n < 1 || !out) return BKFAC_EINVAL;
+  if (dense_path(f, n)) return BKFAC_EINVAL;
+  const UpdatePlan p = plan_update(f, n, f->r);
+  out[0] = (int64_t)p.o_M;
+  out[1] = (int64_t)p.o_Q;
+  out[2] = (int64_t)p.o_L;
+  out[3] = (int64_t)p.o_lam;
+  out[4] = (int64_t)p.o_P;
+  out[5] = p.ldm;
+  out[6] = p.ldq;
+  out[7] = (int64_t)p.o_sw;
+  return BKFAC_OK;
+}
+
+}  // extern "C"

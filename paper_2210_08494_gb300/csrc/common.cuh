@@ -1,0 +1,194 @@
+// common.cuh -- shared definitions of libbkfac (GB300, sm_103a).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bkfac.h"
+
+namespace bkfac {
+
+// ---------------------------------------------------------------------------
+// Device status word.  Kernels record the first error with atomicCAS and
+// never trap; bkfac_status() reads and clears it.
+// ---------------------------------------------------------------------------
+extern __device__ int g_status;
+
+__device__ __forceinline__ void report(int code) { atomicCAS(&g_status, 0, code); }
+
+// ---------------------------------------------------------------------------
+// Precision traits
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Eps;
+template <>
+struct Eps<double> {
+  static constexpr double u = 1.1102230246251565e-16;  // 2^-53
+};
+template <>
+struct Eps<float> {
+  static constexpr double u = 5.9604644775390625e-08;  // 2^-24
+};
+
+__device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+template <typename T>
+__device__ __forceinline__ T ld_round(const T* p, bool rnd) {
+  return *p;
+}
+template <>
+__device__ __forceinline__ float ld_round<float>(const float* p, bool rnd) {
+  float v = *p;
+  return rnd ? round_bf16(v) : v;
+}
+
+__host__ __device__ __forceinline__ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+__host__ __device__ __forceinline__ int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
+
+// ---------------------------------------------------------------------------
+// Generic SIMT GEMM description (see gemm.cu).
+//   C[m, n] = sum_k A(m, k) B(k, n), k over two concatenated segments
+//   A(m, k) = a_kmaj ? A[m*lda + k] : A[m + k*lda]
+//   B(k, n) = b_kmaj ? B[n*ldb + k] : B[k*ldb + n]
+//   epilogue: out = alpha * rs[m] * cs[n] * acc + beta * ds[n] * D(m, n)
+//   (rs, cs, ds may be null = 1; beta_dev, when set, replaces beta)
+//   C and D: c_rowmaj ? C[m*ldc + n] : C[m + n*ldc]
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+  int M, N, K0, K1;
+  const void* A0;
+  int64_t lda0;
+  const void* A1;
+  int64_t lda1;
+  const void* B0;
+  int64_t ldb0;
+  const void* B1;
+  int64_t ldb1;
+  bool a_kmaj, b_kmaj, c_rowmaj, round_bf16;
+  void* C;
+  int64_t ldc;
+  const void* D;
+  int64_t ldd;
+  double alpha, beta;
+  const double* beta_dev;
+  const double* rs;
+  const double* cs;
+  const double* ds;
+  int splits;      // split-K count (1 = direct epilogue)
+  int k_chunk;     // K elements per split (multiple of the tile depth)
+  void* partial;   // splits * M * N accumulators when splits > 1
+};
+
+enum DType { DT_F64 = 0, DT_F32 = 1 };
+
+// launchers implemented in gemm.cu; return a cudaError_t
+// in_t: element type of A/B; acc_t: accumulator; out_t: C/D element type
+int gemm_run(const GemmArgs& g, DType in_t, DType acc_t, DType out_t, cudaStream_t s);
+// suggested split count for a long-K product with small output
+int gemm_pick_splits(int M, int N, int K, int sm_count);
+
+// ---------------------------------------------------------------------------
+// Small dense kernels (small.cu)
+// ---------------------------------------------------------------------------
+// max_j ||x_j||^2 over the n columns of a d x n column-major matrix -> *out (double)
+int launch_colnorm_max(const void* X, int64_t ldx, int d, int n, DType t, double* out, cudaStream_t s);
+// thresholded Cholesky of an n x n FP64 Gram (column-major, ld n): upper R (n x n, ld n);
+// pivot j dropped (row j of R zero) when s_j <= thr_rel * (*scale).  scale may be null (= 1).
+int launch_chol(const double* Gm, int n, double* R, double thr_rel, const double* scale, cudaStream_t s);
+// inverse of the upper-triangular R (zero rows = dropped pivots -> zero rows/cols of Rinv)
+int launch_trinv(const double* R, int n, void* Rinv, DType t, cudaStream_t s);
+
+struct CoreArgs {
+  int k, n, N;            // old rank, batch width, core size N = k + n
+  int rows_pad, cols_pad; // L is rows_pad x cols_pad, column-major, ld = rows_pad
+  double rho, c;
+  const double* sigma;    // k values
+  const void* M;          // k x n, column-major, ld = ldm (type of U)
+  int64_t ldm;
+  const double* R1;       // n x n upper, ld n
+  const double* R2;       // n x n upper, ld n
+  void* L;                // output (Jacobi type)
+  double* colnorm2;       // cols_pad squared column norms (output)
+};
+int launch_assemble_core(const CoreArgs& a, DType m_t, DType j_t, cudaStream_t s);
+
+// dense path: F = [U diag(sqrt(rho sigma)), sqrt(c) X] (d x (k+n) into rows_pad x cols_pad)
+struct DenseArgs {
+  int d, k, n, rows_pad, cols_pad;
+  double rho, c;
+  const void* U;
+  int64_t ldu;
+  const double* sigma;
+  const void* X;
+  int64_t ldx;
+  void* F;
+  double* colnorm2;
+};
+int launch_assemble_dense(const DenseArgs& a, DType u_t, DType j_t, cudaStream_t s);
+
+// reorth: L = R diag(sqrt(sigma)) (k x k into rows_pad x cols_pad)
+int launch_assemble_reorth(const double* R, const double* sigma, int k, int rows_pad, int cols_pad, void* L,
+                           double* colnorm2, DType j_t, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Jacobi (jacobi.cu): one-sided block Jacobi on the columns of W (rows x cols_pad,
+// column-major, ld = rows_pad), one thread-block cluster per problem.
+// ---------------------------------------------------------------------------
+struct JacobiProblem {
+  void* W;
+  int rows, rows_pad, cols_pad, b;   // cols_pad = 2 * C * b
+  const double* colnorm2;            // cols_pad squared column norms of the input
+  int* sweeps_out;                   // optional
+};
+constexpr int kMaxJacobiProblems = 64;
+struct JacobiBatch {
+  JacobiProblem p[kMaxJacobiProblems];
+};
+// probs: host array of nprob <= kMaxJacobiProblems problems sharing the cluster size C
+// (passed by value as a kernel parameter, so the launch can be captured in a graph)
+int launch_jacobi(const JacobiProblem* probs, int nprob, int C, DType j_t, double tol, int max_sweeps,
+                  cudaStream_t s);
+// shared memory bytes one CTA needs for a problem
+size_t jacobi_smem_bytes(int b, int rows_pad, DType j_t);
+// choose cluster size and block width for a problem
+void jacobi_plan(int rows, int cols, DType j_t, int* C, int* b, int* rows_pad, int* cols_pad);
+
+// sort / output: lambda_i = ||w_i||^2 for the first `cols` columns, descending;
+// V[:, rank] = w_i / ||w_i|| (type out_t, rows x r_out, ld ldv) for rank < r_out,
+// sig[rank] = lambda_i, lam_sorted[rank] = lambda_i (optional)
+struct SortArgs {
+  const void* W;
+  int rows, rows_pad, cols;
+  int r_out;
+  void* V;
+  int64_t ldv;
+  double* sig;           // r_sig values written (rank < r_out), zero-filled up to r_sig
+  int r_sig;
+  double* lam_sorted;    // optional, cols values
+  const double* colnorm2; // cols_pad squared column norms of the Jacobi input
+  int cols_pad;
+};
+int launch_sort_output(const SortArgs& a, DType j_t, DType out_t, cudaStream_t s);
+
+// U[:, j] = Unew[:, j] for j < r_new, zero for r_new <= j < r
+int launch_finalize(void* U, int64_t ldu, const void* Unew, int64_t ldn, int d, int r_new, int r, DType t,
+                    cudaStream_t s);
+
+// apply coefficients: cA = 1/(sig+lamA') - 1/lamA' (with optional continuation shift), etc.
+struct ApplyCoefArgs {
+  const double* sigA;
+  int kA;
+  const double* sigG;
+  int kG;
+  double lamA, lamG;
+  int continuation;
+  double* cA;        // kA: C_A
+  double* cG;        // kG: C_G
+  double* cA_over;   // kA: C_A / lamG'
+  double* cG_over;   // kG: C_G / lamA'
+  double* alpha;     // 1: 1 / (lamA' lamG')
+};
+int launch_apply_coefs(const ApplyCoefArgs& a, cudaStream_t s);
+
+}  // namespace bkfac

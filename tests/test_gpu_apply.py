@@ -1,0 +1,77 @@
+"""GPU parity of the damped inverse application (Algorithm 1, K-FAC identity
+of Eq. (4)) through the C ABI, against the FP64 CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2210_08494_gb300 import bkfac, synth
+from tests.parity_util import rel
+
+pytestmark = pytest.mark.gpu
+
+TOL = {bkfac.F64: 1e-10, bkfac.F32: 1e-4, bkfac.MIXED_BF16: 2e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    bkfac.load()
+    bkfac.bkfac_status()
+    yield
+
+
+def make_factor(d, r, k, dtype, seed):
+    f = bkfac.Factor(d, r, dtype)
+    if k:
+        Ut = synth.orthonormal_columns(d, k, seed)
+        sig = np.sort(2.0 * np.exp(-np.linspace(0, 5, k)))[::-1].copy()
+        f.load_state(torch.from_numpy(Ut).to(f.torch_dtype).cuda(), torch.from_numpy(sig).cuda())
+    U, s = f.state()
+    return f, U.double().cpu().numpy(), s.cpu().numpy()
+
+
+def run_apply(oracle, dA, rA, kA, dG, rG, kG, dtype, lamA=0.1, lamG=0.05, flags=0, inplace=False, seed=1):
+    fA, UA, sA = make_factor(dA, rA, kA, dtype, seed)
+    fG, UG, sG = make_factor(dG, rG, kG, dtype, seed + 1)
+    Gn = synth.gradient(dG, dA, seed + 2, 0)
+    G = bkfac.grad_tensor(dG, dA, fA.torch_dtype)
+    G.copy_(torch.from_numpy(Gn))
+    Gr = G.double().cpu().numpy()
+    S = G if inplace else bkfac.grad_tensor(dG, dA, fA.torch_dtype)
+    bkfac.bkfac_apply(fA, fG, lamA, lamG, G, S, flags=flags)
+    st = bkfac.bkfac_status()
+    assert st == bkfac.OK, bkfac.strerror(st)
+    So = oracle.apply(UA, sA, lamA, UG, sG, lamG, Gr, continuation=bool(flags & bkfac.SPECTRUM_CONTINUATION))
+    err = rel(S.double().cpu().numpy(), So)
+    assert err < TOL[dtype], err
+    return err
+
+
+@pytest.mark.parametrize("dtype", [bkfac.F64, bkfac.F32, bkfac.MIXED_BF16])
+def test_apply_ragged_shapes(oracle, dtype):
+    err = run_apply(oracle, 301, 24, 24, 130, 16, 16, dtype)
+    print(f"apply dtype {dtype}: {err:.2e}")
+
+
+def test_apply_config1_f64(oracle):
+    run_apply(oracle, 512, 64, 64, 256, 64, 64, bkfac.F64, lamA=0.1, lamG=0.1)
+
+
+def test_apply_spectrum_continuation(oracle):
+    run_apply(oracle, 200, 12, 12, 90, 8, 8, bkfac.F64, flags=bkfac.SPECTRUM_CONTINUATION)
+
+
+def test_apply_in_place(oracle):
+    run_apply(oracle, 160, 10, 10, 70, 6, 6, bkfac.F32, inplace=True)
+
+
+@pytest.mark.parametrize("kA,kG", [(0, 5), (7, 0), (0, 0), (3, 5)])
+def test_apply_partial_ranks(oracle, kA, kG):
+    """r_cur below r (and empty factors: S = G / (lamA lamG))."""
+    run_apply(oracle, 100, 9, kA, 60, 7, kG, bkfac.F64)
+
+
+def test_apply_config2_full_size(oracle):
+    """Config-2 shape: G 4096 x 4097 FP32 with r_A = r_G = 256, lambda = 1e-2."""
+    err = run_apply(oracle, 4097, 256, 256, 4096, 256, 256, bkfac.F32, lamA=1e-2, lamG=1e-2)
+    print(f"config-2 apply relative error {err:.2e}")

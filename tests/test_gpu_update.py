@@ -1,0 +1,242 @@
+"""GPU parity of the B-KFAC update (Algorithm 4 via Algorithm 3) and of the
+re-orthonormalisation, through the C ABI, against the FP64 CPU oracle.
+
+One-step parity: before each step the oracle starts from the GPU's state
+(exact values up-cast to float64) and both sides consume the same seeded
+batch (rounded to the path's dtype), so each step's tolerance applies to that
+step alone.  Trajectory parity: both run free from the same first batch.
+
+Tolerances (relative Frobenius): 1e-10 for the FP64 path, 1e-4 for the FP32
+path, 2e-2 for the mixed BF16 path (operand rounding u_bf16 = 2^-8 in each
+tall-skinny product, FP32 accumulation).
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2210_08494_gb300 import bkfac, synth
+from tests.parity_util import lowrank_rel_err, orth_err, rel, truncation_gap
+
+pytestmark = pytest.mark.gpu
+
+TOL = {bkfac.F64: 1e-10, bkfac.F32: 1e-4, bkfac.MIXED_BF16: 2e-2}
+ORTH = {bkfac.F64: 1e-12, bkfac.F32: 2e-5, bkfac.MIXED_BF16: 2e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    bkfac.load()
+    bkfac.bkfac_status()
+    yield
+
+
+def to_dev(Xt, f):
+    """(n, d) float64 numpy batch -> (n, d) device view with padded rows, f's dtype."""
+    n, d = Xt.shape
+    t = bkfac.cols_tensor(n, d, f.torch_dtype)
+    t.copy_(torch.from_numpy(Xt))
+    return t
+
+
+def rounded(Xt, f):
+    """The exact values the GPU receives, as float64."""
+    return torch.from_numpy(Xt).to(f.torch_dtype).double().numpy()
+
+
+def gpu_state(f):
+    U, s = f.state()
+    return U.double().cpu().numpy(), s.cpu().numpy()
+
+
+def check_status():
+    st = bkfac.bkfac_status()
+    assert st == bkfac.OK, bkfac.strerror(st)
+
+
+def one_step_parity(oracle, d, r, n, dtype, rho=0.95, steps=4, alpha=1.5, seed=1, flags=0):
+    f = bkfac.Factor(d, r, dtype, flags=flags)
+    dense = r + n >= d
+    tol = TOL[dtype]
+    X0 = synth.powerlaw_batch(d, n, alpha, seed, 0)
+    bkfac.bkfac_init(f, to_dev(X0, f))
+    check_status()
+    Uo, so, info = oracle.init(rounded(X0, f), r, dense=dense)
+    Ug, sg = gpu_state(f)
+    k = info["r_new"]
+    assert f.r_cur == k
+    assert rel(sg, so[:k]) < tol
+    assert lowrank_rel_err(Ug, sg, Uo[:k], so[:k]) < tol
+    worst = 0.0
+    for t in range(1, steps + 1):
+        Ug, sg = gpu_state(f)
+        X = synth.powerlaw_batch(d, n, alpha, seed, t)
+        bkfac.bkfac_update(f, to_dev(X, f), rho)
+        check_status()
+        upd = oracle.update_dense if dense else oracle.update
+        Uo, so, info = upd(Ug, sg, Ug.shape[0], rounded(X, f), rho, r)
+        k = info["r_new"]
+        assert f.r_cur == k
+        U2, s2 = gpu_state(f)
+        es = rel(s2, so[:k])
+        er = lowrank_rel_err(U2, s2, Uo[:k], so[:k])
+        worst = max(worst, es, er)
+        assert es < tol, (t, es)
+        assert er < tol, (t, er)
+        assert orth_err(U2[s2 > 0]) < ORTH[dtype]
+    return f, worst
+
+
+@pytest.mark.parametrize("d,r,n", [(300, 24, 20), (65, 7, 3), (512, 64, 32)])
+def test_update_f64_one_step(oracle, d, r, n):
+    one_step_parity(oracle, d, r, n, bkfac.F64, steps=5)
+
+
+@pytest.mark.parametrize("d,r,n", [(600, 48, 40), (257, 16, 33)])
+def test_update_f32_one_step(oracle, d, r, n):
+    one_step_parity(oracle, d, r, n, bkfac.F32, alpha=1.2, steps=4)
+
+
+def test_update_f32_with_fp64_eigensolve(oracle):
+    one_step_parity(oracle, 400, 32, 24, bkfac.F32, alpha=1.2, steps=3, flags=bkfac.FLAG_EIG_FP64)
+
+
+def test_update_mixed_one_step(oracle):
+    _, worst = one_step_parity(oracle, 700, 40, 48, bkfac.MIXED_BF16, alpha=1.2, steps=3)
+    print(f"mixed one-step worst relative error {worst:.3e}")
+
+
+@pytest.mark.parametrize("dtype", [bkfac.F64, bkfac.F32])
+def test_dense_path_small_factor(oracle, dtype):
+    """r + n >= d (the 10-way output layer's Gamma): explicit K, exact EVD."""
+    one_step_parity(oracle, 10, 10, 32, dtype, steps=3)
+
+
+def test_dense_path_wider(oracle):
+    one_step_parity(oracle, 90, 64, 40, bkfac.F64, steps=2)
+
+
+def test_init_keeps_rank_n_when_n_below_r(oracle):
+    f, _ = one_step_parity(oracle, 200, 30, 8, bkfac.F64, steps=3)
+    assert f.r_cur == 30
+
+
+def test_trajectory_f64_config1(oracle):
+    """Config-1 shape (d=512, r=64, n=32, rho=0.95, alpha=1.5), free-running for
+    20 steps on both sides."""
+    d, r, n, rho = 512, 64, 32, 0.95
+    f = bkfac.Factor(d, r, bkfac.F64)
+    X0 = synth.powerlaw_batch(d, n, 1.5, 1000, 0)
+    bkfac.bkfac_init(f, to_dev(X0, f))
+    Uo, so, info = oracle.init(X0, r)
+    k = info["r_new"]
+    min_gap = np.inf
+    for t in range(1, 21):
+        X = synth.powerlaw_batch(d, n, 1.5, 1000, t)
+        bkfac.bkfac_update(f, to_dev(X, f), rho)
+        Uo, so, info = oracle.update(Uo[:k], so[:k], k, X, rho, r)
+        k = info["r_new"]
+        min_gap = min(min_gap, truncation_gap(so, min(r, len(so) - 1)))
+    check_status()
+    Ug, sg = gpu_state(f)
+    err = lowrank_rel_err(Ug, sg, Uo[:k], so[:k])
+    print(f"trajectory error after 20 steps {err:.3e} (min truncation gap {min_gap:.2e})")
+    assert err < 1e-9
+
+
+def test_update_in_span_drops_residual(oracle):
+    """X = U C: the residual vanishes, its pivots are dropped, the span is kept."""
+    d, r, n = 256, 16, 8
+    f = bkfac.Factor(d, r, bkfac.F64)
+    X0 = synth.powerlaw_batch(d, 32, 1.5, 3, 0)
+    bkfac.bkfac_init(f, to_dev(X0, f))
+    Ug, sg = gpu_state(f)
+    C = np.random.default_rng(0).standard_normal((n, Ug.shape[0]))
+    X = C @ Ug
+    bkfac.bkfac_update(f, to_dev(X, f), 0.9)
+    check_status()
+    Uo, so, info = oracle.update(Ug, sg, Ug.shape[0], X, 0.9, r)
+    U2, s2 = gpu_state(f)
+    assert lowrank_rel_err(U2, s2, Uo[: f.r_cur], so[: f.r_cur]) < 1e-10
+    assert np.abs(U2 - (U2 @ Ug.T) @ Ug).max() < 1e-10
+
+
+def test_update_duplicate_columns(oracle):
+    d, r, n = 300, 20, 12
+    f = bkfac.Factor(d, r, bkfac.F32)
+    X0 = synth.powerlaw_batch(d, n, 1.2, 4, 0)
+    bkfac.bkfac_init(f, to_dev(X0, f))
+    Ug, sg = gpu_state(f)
+    X = synth.powerlaw_batch(d, n, 1.2, 4, 1)
+    X[6:] = X[:6]
+    bkfac.bkfac_update(f, to_dev(X, f), 0.95)
+    check_status()
+    Uo, so, info = oracle.update(Ug, sg, Ug.shape[0], rounded(X, f), 0.95, r)
+    U2, s2 = gpu_state(f)
+    k = f.r_cur
+    assert rel(s2, so[:k]) < 1e-4
+    assert lowrank_rel_err(U2, s2, Uo[:k], so[:k]) < 1e-4
+
+
+@pytest.mark.parametrize("dtype", [bkfac.F32, bkfac.MIXED_BF16])
+def test_reorth_restores_orthonormality(oracle, dtype):
+    d, r = 500, 40
+    f = bkfac.Factor(d, r, dtype)
+    Ut = synth.orthonormal_columns(d, r, 5)
+    noisy = Ut + 1e-3 * np.random.default_rng(1).standard_normal(Ut.shape)
+    sig = np.sort(np.exp(-np.linspace(0, 4, r)))[::-1].copy()
+    f.load_state(torch.from_numpy(noisy).to(f.torch_dtype).cuda(), torch.from_numpy(sig).cuda())
+    Uin, sin = gpu_state(f)
+    bkfac.bkfac_reorth(f)
+    check_status()
+    Uo, so = oracle.reorth(Uin, sin)
+    U2, s2 = gpu_state(f)
+    assert orth_err(U2) < 2e-5
+    assert rel(s2, so) < 1e-4
+    assert lowrank_rel_err(U2, s2, Uo, so) < 1e-4
+
+
+def test_nonfinite_input_sets_status():
+    d, r, n = 128, 8, 8
+    f = bkfac.Factor(d, r, bkfac.F32)
+    X = synth.powerlaw_batch(d, n, 1.5, 6, 0)
+    X[2, 5] = np.nan
+    bkfac.bkfac_init(f, to_dev(X, f))
+    assert bkfac.bkfac_status() == bkfac.ENONFINITE
+    assert bkfac.bkfac_status() == bkfac.OK  # cleared by the read
+
+
+def test_invalid_arguments_are_rejected_before_launch():
+    f = bkfac.Factor(64, 8, bkfac.F32)
+    X = bkfac.cols_tensor(4, 64, torch.float32)
+    with pytest.raises(bkfac.BkfacError) as e:
+        bkfac.bkfac_update(f, X, 0.95)  # r_cur == 0: init first
+    assert e.value.code == bkfac.EINVAL
+    with pytest.raises(bkfac.BkfacError) as e:
+        bkfac.bkfac_init(f, X, ws=bkfac.workspace(64))
+    assert e.value.code == bkfac.EWORKSPACE
+    with pytest.raises(bkfac.BkfacError) as e:
+        bkfac.bkfac_init(f, torch.zeros(4, 63, device="cuda"))  # ld 63 floats is not 16-byte aligned
+    assert e.value.code == bkfac.EINVAL
+    assert bkfac.bkfac_status() == bkfac.OK
+
+
+def test_config2_full_size_one_step(oracle):
+    """Config-2 shape (A factor: d = 4097, r = n = 256, FP32, rho = 0.95, alpha =
+    1.2), in the launch configuration the benchmark times: init on the GPU,
+    then one update compared with the oracle started from the GPU state."""
+    d, r, n, rho = 4097, 256, 256, 0.95
+    f = bkfac.Factor(d, r, bkfac.F32)
+    X0 = synth.powerlaw_batch(d, n, 1.2, 2000, 0)
+    bkfac.bkfac_init(f, to_dev(X0, f))
+    check_status()
+    Ug, sg = gpu_state(f)
+    X = synth.powerlaw_batch(d, n, 1.2, 2000, 1)
+    bkfac.bkfac_update(f, to_dev(X, f), rho)
+    check_status()
+    Uo, so, info = oracle.update(Ug, sg, Ug.shape[0], rounded(X, f), rho, r)
+    U2, s2 = gpu_state(f)
+    es, er = rel(s2, so), lowrank_rel_err(U2, s2, Uo, so)
+    print(f"config-2 one-step: sigma {es:.2e} reconstruction {er:.2e} orth {orth_err(U2):.2e}")
+    assert es < 1e-4 and er < 1e-4
+    assert orth_err(U2) < 1e-4
