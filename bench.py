@@ -1,0 +1,391 @@
+"""Benchmark of the B-KFAC preconditioning hot path on one GB300.
+
+Workload (the one-wide-FC-layer configuration): forward factor A at d = 4097
+(4096 inputs + bias), backward factor Gamma at d = 4096, rank r = 256, n = 256
+new columns per step, rho = 0.95, lambda = 1e-2, FP32 plain per-factor path.
+One step = Brand update of A + Brand update of Gamma + damped inverse
+application to a fresh 4096 x 4097 FP32 gradient.  Inputs are seeded
+synthetic power-law batches (exponent 1.2) and N(0, 1) gradients, resident in
+HBM before the timed region (config["inputs"]).
+
+Metric: factor updates per second (two per step); the preconditioned
+gradients per second are reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl bkfac|reference]
+Under torchrun (N > 1) every rank runs the same per-GPU workload on its own
+layer (independent replicas, weak scaling); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "K-factor Brand updates/sec + preconditioned grads/sec (1 GB300), batched vs plain"
+D_A, D_G, R, N, RHO, LAM, ALPHA = 4097, 4096, 256, 256, 0.95, 1e-2, 1.2
+WORKLOAD = "one wide FC layer: A d=4097, Gamma d=4096, r=256, n=256, rho=0.95, lambda=1e-2, G 4096x4097"
+POOL_X, POOL_G = 8, 3
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=5)
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# --------------------------------------------------------------------------- reference arm: the oracle on the host
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2210_08494_gb300 import synth
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    step_cap_s = float(os.environ.get("BKFAC_REF_BUDGET_S", "150"))
+    seedA, seedG = synth.factor_seed(2, 0, "A"), synth.factor_seed(2, 0, "G")
+    XA = [synth.powerlaw_batch(D_A, N, ALPHA, seedA, t) for t in range(2)]
+    XG = [synth.powerlaw_batch(D_G, N, ALPHA, seedG, t) for t in range(2)]
+    G = synth.gradient(D_G, D_A, seedA, 0)
+    UA, sA, iA = oracle.init(XA[0], R)
+    UG, sG, iG = oracle.init(XG[0], R)
+    times = []
+    t_all = time.time()
+    total = max(1, args.warmup) + args.steps
+    for i in range(total):
+        t0 = time.perf_counter()
+        UA2, sA2, _ = oracle.update(UA, sA, iA["r_new"], XA[1], RHO, R)
+        UG2, sG2, _ = oracle.update(UG, sG, iG["r_new"], XG[1], RHO, R)
+        oracle.apply(UA2, sA2, LAM, UG2, sG2, LAM, G)
+        dt = time.perf_counter() - t0
+        if i >= total - args.steps:
+            times.append(dt)
+        if time.time() - t_all > step_cap_s and len(times) >= 1:
+            break
+    t_step = float(np.mean(times))
+    value = 2.0 / t_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "factor-updates/s", "n_gpus": world,
+        "steps": len(times), "warmup": total - len(times) if len(times) < args.steps else max(1, args.warmup),
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "path": "FP64 CPU oracle (Householder QR, two-sided Jacobi, direct apply)"},
+        "preconditioned_grads_per_s": 1.0 / t_step,
+        "cpu_baseline": {"value": value, "unit": "factor-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{len(times)} full step(s): 2 factor updates + 1 apply at the full shapes"},
+        "e2e": {"value": value, "unit": "factor-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample():
+    """The oracle timed on the host cores on one full step (about 10-30 s)."""
+    import oracle
+    from paper_2210_08494_gb300 import synth
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    seedA, seedG = synth.factor_seed(2, 0, "A"), synth.factor_seed(2, 0, "G")
+    XA = [synth.powerlaw_batch(D_A, N, ALPHA, seedA, t) for t in range(2)]
+    XG = [synth.powerlaw_batch(D_G, N, ALPHA, seedG, t) for t in range(2)]
+    G = synth.gradient(D_G, D_A, seedA, 0)
+    UA, sA, iA = oracle.init(XA[0], R)
+    UG, sG, iG = oracle.init(XG[0], R)
+    t0 = time.perf_counter()
+    UA2, sA2, _ = oracle.update(UA, sA, iA["r_new"], XA[1], RHO, R)
+    UG2, sG2, _ = oracle.update(UG, sG, iG["r_new"], XG[1], RHO, R)
+    oracle.apply(UA2, sA2, LAM, UG2, sG2, LAM, G)
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 / dt, "unit": "factor-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"1 full step (2 factor updates at d=4097/4096, r=n=256 + 1 apply to 4096x4097), {dt:.1f} s"}
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+
+def algorithmic_work(phase, ms, counts, sweeps):
+    """Algorithmic bytes / flops per launch of a phase at the benchmark shapes (both factors)."""
+    d = (D_A + D_G) / 2.0
+    Nc = R + N
+    if phase == "jacobi":
+        # one-sided Jacobi, FP32: per sweep every column pair costs 3 dot products and a
+        # rotation over Nc rows = 12 * Nc flops; per launch (one factor) x sweeps
+        flops = sweeps * (Nc * (Nc - 1) / 2.0) * 12.0 * Nc
+        return {"bound": "alu", "flops": flops}
+    if phase == "apply_pass2":
+        return {"bound": "hbm", "bytes": 2.0 * D_G * D_A * 4, "flops": 2.0 * D_G * D_A * 2 * R}
+    if phase == "apply_pass1":
+        return {"bound": "hbm", "bytes": D_G * D_A * 4 + D_A * R * 4, "flops": 2.0 * D_G * D_A * R}
+    if phase == "chol":
+        return {"bound": "alu64", "flops": N ** 3 / 3.0}
+    if phase == "gram":
+        return {"bound": "alu64", "flops": 2.0 * d * N * N}
+    if phase == "trinv":
+        return {"bound": "alu", "flops": N ** 3 / 3.0}
+    return None
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    from paper_2210_08494_gb300 import bkfac, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    bkfac.load()
+    bkfac.bkfac_status()
+    layer = rank  # each rank preconditions its own layer (independent replicas)
+    seedA, seedG = synth.factor_seed(2, layer, "A"), synth.factor_seed(2, layer, "G")
+    fA = bkfac.Factor(D_A, R, bkfac.F32, device=dev)
+    fG = bkfac.Factor(D_G, R, bkfac.F32, device=dev)
+
+    def dev_cols(Xt, f):
+        t = bkfac.cols_tensor(Xt.shape[0], Xt.shape[1], torch.float32, dev)
+        t.copy_(torch.from_numpy(Xt))
+        return t
+
+    XA = [dev_cols(synth.powerlaw_batch(D_A, N, ALPHA, seedA, t), fA) for t in range(POOL_X)]
+    XG = [dev_cols(synth.powerlaw_batch(D_G, N, ALPHA, seedG, t), fG) for t in range(POOL_X)]
+    gen = torch.Generator(device=dev).manual_seed(seedA + 500)
+    Gs = []
+    for _ in range(POOL_G):
+        g = bkfac.grad_tensor(D_G, D_A, torch.float32, dev, zero=False)
+        g.normal_(generator=gen)
+        Gs.append(g)
+    S = bkfac.grad_tensor(D_G, D_A, torch.float32, dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    bkfac.bkfac_init(fA, XA[0])
+    bkfac.bkfac_init(fG, XG[0])
+    stream = torch.cuda.current_stream()
+
+    def step(t):
+        bkfac.bkfac_update(fA, XA[1 + t % (POOL_X - 1)], RHO)
+        bkfac.bkfac_update(fG, XG[1 + t % (POOL_X - 1)], RHO)
+        bkfac.bkfac_apply(fA, fG, LAM, LAM, Gs[t % POOL_G], S)
+
+    for t in range(args.warmup):
+        step(t)
+    torch.cuda.synchronize()
+    st = bkfac.bkfac_status()
+    if st != bkfac.OK:
+        raise RuntimeError(f"device status after warm-up: {bkfac.strerror(st)}")
+
+    # ---- timed region: K steps, L2 flushed between steps (outside the events)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    _, launches0 = bkfac.bkfac_trace_read()
+    bkfac.bkfac_trace_enable(True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for t in range(args.steps):
+            flush.zero_()
+            evs[t][0].record(stream)
+            step(args.warmup + t)
+            evs[t][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    trace, launches1 = bkfac.bkfac_trace_read()
+    bkfac.bkfac_trace_enable(False)
+    st = bkfac.bkfac_status()
+    if st != bkfac.OK:
+        raise RuntimeError(f"device status after timed region: {bkfac.strerror(st)}")
+    ms_total = float(sum(a.elapsed_time(b) for a, b in evs))
+    if world > 1:
+        tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    steps_per_s = 1000.0 / ms_step
+    value = 2.0 * steps_per_s * world
+    gpu_launches = launches1 - launches0
+
+    # ---- roofline of the dominant phase (CUDA events around each phase, same stream)
+    sweeps = int(fA.ws(N)[bkfac.bkfac_debug_offsets(fA, N)[7]:][:4].view(torch.int32).item())
+    peaks, peak_src = measured_peaks()
+    dom = max(trace.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_cnt) = dom
+    work = algorithmic_work(dom_name, dom_ms, dom_cnt, sweeps)
+    roof = None
+    if work is not None and dom_cnt:
+        per_launch_ms = dom_ms / dom_cnt
+        if work["bound"] == "hbm":
+            ach = work["bytes"] / (per_launch_ms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_src}
+        else:
+            ach = work["flops"] / (per_launch_ms * 1e-3) / 1e12
+            if work["bound"] == "alu":
+                pk = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x FMA x max SM clock
+                src = "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"
+            else:
+                pk = 1.25
+                src = "nominal FP64 1.25 TFLOP/s"
+            roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                    "traffic": None, "peak_source": src}
+        roof["kernel"] = dom_name
+        roof["launch_ms"] = per_launch_ms
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        ldA, ldG, ldg = fA.U.stride(0), fG.U.stride(0), Gs[0].stride(0)
+        hXA = torch.empty(N, ldA, dtype=torch.float32, pin_memory=True)
+        hXG = torch.empty(N, ldG, dtype=torch.float32, pin_memory=True)
+        hG = torch.empty(D_G, ldg, dtype=torch.float32, pin_memory=True)
+        hXA[:, :D_A].copy_(XA[1])
+        hXG[:, :D_G].copy_(XG[1])
+        hG[:, :D_A].copy_(Gs[0])
+        hS = torch.empty(D_G, ldg, dtype=torch.float32, pin_memory=True)
+        bXA = torch.zeros(N, ldA, dtype=torch.float32, device=dev)
+        bXG = torch.zeros(N, ldG, dtype=torch.float32, device=dev)
+        bG = torch.zeros(D_G, ldg, dtype=torch.float32, device=dev)
+        bS = torch.zeros(D_G, ldg, dtype=torch.float32, device=dev)
+        dXA, dXG, dG, dS = bXA[:, :D_A], bXG[:, :D_G], bG[:, :D_A], bS[:, :D_A]
+        e2e_steps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(e2e_steps):
+            bXA.copy_(hXA, non_blocking=True)
+            bXG.copy_(hXG, non_blocking=True)
+            bG.copy_(hG, non_blocking=True)
+            bkfac.bkfac_update(fA, dXA, RHO)
+            bkfac.bkfac_update(fG, dXG, RHO)
+            bkfac.bkfac_apply(fA, fG, LAM, LAM, dG, dS)
+            hS.copy_(bS, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1) / e2e_steps
+        e2e = {"value": 2.0 * 1000.0 / ms_e2e * world, "unit": "factor-updates/s",
+               "h2d_bytes_per_step": int((hXA.numel() + hXG.numel() + hG.numel()) * 4),
+               "d2h_bytes_per_step": int(hS.numel() * 4), "ms_per_step": ms_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "factor-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "path": "plain FP32 per-factor calls", "layers_per_gpu": 1,
+                       "inputs": "resident in HBM; L2 flushed (256 MB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "preconditioned_grads_per_s": steps_per_s * world,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clk.summary(),
+            "phases_ms_per_step": {k: v[0] / args.steps for k, v in trace.items() if v[1]},
+            "jacobi_sweeps": sweeps,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="bkfac", choices=["bkfac", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup) if args.impl == "bkfac" else args.warmup
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

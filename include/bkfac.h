@@ -194,6 +194,22 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
  * for the dense path (which has no M, Q, R). */
 int bkfac_debug_offsets(const bkfac_factor* f, int n, int64_t out[8]);
 
+/* ---- tracing ---------------------------------------------------------------
+ * Optional per-phase timing: while enabled, each phase of every call records
+ * a CUDA event pair on the call's stream (not while the stream is being
+ * captured into a graph).  Host-side state shared by all streams of the
+ * process; not meant for concurrent use from several host threads.
+ *   bkfac_trace_enable(on)  turns tracing on/off and clears the accumulators
+ *   bkfac_trace_read(ms, count, nmax, launches)  waits for the recorded
+ *       events, accumulates, and copies per-phase totals (milliseconds,
+ *       number of timed phase instances) for up to nmax phases; *launches
+ *       receives the number of kernels the library has launched since load.
+ *       Returns the number of phases, or minus an error code.
+ *   bkfac_trace_phase_name(id)  static name of phase id. */
+int bkfac_trace_enable(int on);
+int bkfac_trace_read(double* ms, int64_t* count, int nmax, int64_t* launches);
+const char* bkfac_trace_phase_name(int id);
+
 /* ---- batched calls: all factors of all FC layers -------------------------
  * A batch groups the two factors of nlayers layers (uneven d, r) with a
  * common batch width n and dtype.  Each phase of the update and of the apply

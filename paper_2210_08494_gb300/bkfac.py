@@ -90,6 +90,9 @@ def load(build_if_missing: bool = True):
                                         ctypes.POINTER(P), ctypes.POINTER(I64), ctypes.POINTER(D),
                                         ctypes.POINTER(D), U32, I, P], I),
             "bkfac_batch_destroy": ([P], None),
+            "bkfac_trace_enable": ([I], I),
+            "bkfac_trace_read": ([ctypes.POINTER(D), ctypes.POINTER(I64), I, ctypes.POINTER(I64)], I),
+            "bkfac_trace_phase_name": ([I], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name, None)
@@ -108,7 +111,8 @@ def exported_symbols():
     for n in ("bkfac_version", "bkfac_strerror", "bkfac_status", "bkfac_workspace_size",
               "bkfac_apply_workspace_size", "bkfac_init", "bkfac_update", "bkfac_reorth", "bkfac_apply",
               "bkfac_debug_offsets", "bkfac_batch_create", "bkfac_batch_get_factor", "bkfac_batch_update",
-              "bkfac_batch_apply", "bkfac_batch_step_graph", "bkfac_batch_destroy"):
+              "bkfac_batch_apply", "bkfac_batch_step_graph", "bkfac_batch_destroy", "bkfac_trace_enable",
+              "bkfac_trace_read", "bkfac_trace_phase_name"):
         if hasattr(lib, n):
             names.append(n)
     return names
@@ -272,3 +276,26 @@ def bkfac_debug_offsets(f: Factor, n: int):
     out = (ctypes.c_int64 * 8)()
     _check(load().bkfac_debug_offsets(ctypes.byref(f.desc), int(n), out), "bkfac_debug_offsets")
     return list(out)
+
+
+def bkfac_trace_enable(on: bool = True):
+    _check(load().bkfac_trace_enable(1 if on else 0), "bkfac_trace_enable")
+
+
+def bkfac_trace_read():
+    """Per-phase totals since tracing was enabled: {name: (ms, count)}, plus the
+    library's kernel-launch counter."""
+    lib = load()
+    nmax = 64
+    ms = (ctypes.c_double * nmax)()
+    cnt = (ctypes.c_int64 * nmax)()
+    launches = ctypes.c_int64(0)
+    nph = lib.bkfac_trace_read(ms, cnt, nmax, ctypes.byref(launches))
+    if nph < 0:
+        raise BkfacError(-nph, "bkfac_trace_read")
+    out = {lib.bkfac_trace_phase_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(nph)}
+    return out, int(launches.value)
+
+
+def bkfac_launch_count() -> int:
+    return bkfac_trace_read()[1]

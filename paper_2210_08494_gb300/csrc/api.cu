@@ -227,12 +227,17 @@ P* at(void* ws, size_t off) {
   return (P*)((char*)ws + off);
 }
 
-int cuda_rc(int e) { return e == 0 ? BKFAC_OK : BKFAC_ECUDA; }
-
 #define BK_TRY(expr)                     \
   do {                                   \
     int _e = (expr);                     \
     if (_e != 0) return BKFAC_ECUDA;     \
+  } while (0)
+
+// one traced phase: CUDA events around the launches when tracing is enabled
+#define PHASE(ph, expr)                  \
+  do {                                   \
+    TraceScope _ts((ph), s);             \
+    BK_TRY(expr);                        \
   } while (0)
 
 GemmArgs gemm_base() {
@@ -303,7 +308,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     a.ldx = ldx;
     a.F = at<void>(ws, p.o_L);
     a.colnorm2 = at<double>(ws, p.o_cn);
-    BK_TRY(launch_assemble_dense(a, pr.t, pr.jt, s));
+    PHASE(PH_DENSE, launch_assemble_dense(a, pr.t, pr.jt, s));
     JacobiProblem jp;
     jp.W = a.F;
     jp.rows = d;
@@ -312,7 +317,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     jp.b = p.b;
     jp.colnorm2 = a.colnorm2;
     jp.sweeps_out = at<int>(ws, p.o_sw);
-    BK_TRY(launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(d, pr.jt), kMaxSweeps, s));
+    PHASE(PH_JACOBI, launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(d, pr.jt), kMaxSweeps, s));
     SortArgs so;
     so.W = a.F;
     so.rows = d;
@@ -326,10 +331,10 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     so.lam_sorted = at<double>(ws, p.o_lam);
     so.colnorm2 = a.colnorm2;
     so.cols_pad = p.cols_pad;
-    BK_TRY(launch_sort_output(so, pr.jt, pr.t, s));
+    PHASE(PH_SORT, launch_sort_output(so, pr.jt, pr.t, s));
     // columns past r_new are cleared so U holds no stale modes
     if (p.r_new < f->r) {
-      BK_TRY(launch_finalize(f->U, f->ldu, f->U, f->ldu, d, p.r_new, f->r, pr.t, s));
+      PHASE(PH_FINALIZE, launch_finalize(f->U, f->ldu, f->U, f->ldu, d, p.r_new, f->r, pr.t, s));
     }
     return BKFAC_OK;
   }
@@ -344,7 +349,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   double* R1 = at<double>(ws, p.o_R1);
   double* R2 = at<double>(ws, p.o_R2);
   void* Rinv = at<void>(ws, p.o_Rinv);
-  BK_TRY(launch_colnorm_max(X, ldx, d, n, pr.t, scale, s));
+  PHASE(PH_COLNORM, launch_colnorm_max(X, ldx, d, n, pr.t, scale, s));
 
   const void* Pp = X;
   int64_t ldp = ldx;
@@ -365,7 +370,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     g.ldc = p.ldm;
     g.splits = gemm_pick_splits(k, n, d, 152);
     g.partial = part;
-    BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+    PHASE(PH_PROJ, gemm_run(g, pr.t, pr.acc, pr.t, s));
     // P = X - U M  (d x n, K = k)
     GemmArgs h = gemm_base();
     h.M = d;
@@ -384,7 +389,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     h.ldd = ldx;
     h.alpha = -1.0;
     h.beta = 1.0;
-    BK_TRY(gemm_run(h, pr.t, pr.acc, pr.t, s));
+    PHASE(PH_RESID, gemm_run(h, pr.t, pr.acc, pr.t, s));
     Pp = P;
     ldp = p.ldq;
   }
@@ -392,14 +397,14 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   const double ue = pr.bf16 ? 3.90625e-3 : pr.u_t;
   const double thr1 = pr.bf16 ? (2.0 * ue) * (2.0 * ue) : (64.0 * ue) * (64.0 * ue);
   const double thr2 = (64.0 * pr.u_t) * (64.0 * pr.u_t);
-  BK_TRY(run_gram(Pp, ldp, d, n, pr, Gm, part, s));
-  BK_TRY(launch_chol(Gm, n, R1, thr1, scale, s));
-  BK_TRY(launch_trinv(R1, n, Rinv, pr.t, s));
-  BK_TRY(run_trmm(Pp, ldp, d, n, Rinv, pr, Q1, p.ldq, s));
-  BK_TRY(run_gram(Q1, p.ldq, d, n, pr, Gm, part, s));
-  BK_TRY(launch_chol(Gm, n, R2, thr2, nullptr, s));
-  BK_TRY(launch_trinv(R2, n, Rinv, pr.t, s));
-  BK_TRY(run_trmm(Q1, p.ldq, d, n, Rinv, pr, Q, p.ldq, s));
+  PHASE(PH_GRAM, run_gram(Pp, ldp, d, n, pr, Gm, part, s));
+  PHASE(PH_CHOL, launch_chol(Gm, n, R1, thr1, scale, s));
+  PHASE(PH_TRINV, launch_trinv(R1, n, Rinv, pr.t, s));
+  PHASE(PH_TRMM, run_trmm(Pp, ldp, d, n, Rinv, pr, Q1, p.ldq, s));
+  PHASE(PH_GRAM, run_gram(Q1, p.ldq, d, n, pr, Gm, part, s));
+  PHASE(PH_CHOL, launch_chol(Gm, n, R2, thr2, nullptr, s));
+  PHASE(PH_TRINV, launch_trinv(R2, n, Rinv, pr.t, s));
+  PHASE(PH_TRMM, run_trmm(Q1, p.ldq, d, n, Rinv, pr, Q, p.ldq, s));
   // core factor L and its Jacobi eigensolve
   CoreArgs ca;
   ca.k = k;
@@ -416,7 +421,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   ca.R2 = R2;
   ca.L = at<void>(ws, p.o_L);
   ca.colnorm2 = at<double>(ws, p.o_cn);
-  BK_TRY(launch_assemble_core(ca, pr.t, pr.jt, s));
+  PHASE(PH_CORE, launch_assemble_core(ca, pr.t, pr.jt, s));
   JacobiProblem jp;
   jp.W = ca.L;
   jp.rows = p.N;
@@ -425,7 +430,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   jp.b = p.b;
   jp.colnorm2 = ca.colnorm2;
   jp.sweeps_out = at<int>(ws, p.o_sw);
-  BK_TRY(launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(p.N, pr.jt), kMaxSweeps, s));
+  PHASE(PH_JACOBI, launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(p.N, pr.jt), kMaxSweeps, s));
   SortArgs so;
   so.W = ca.L;
   so.rows = p.N;
@@ -440,7 +445,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   so.colnorm2 = ca.colnorm2;
   so.cols_pad = p.cols_pad;
   // sigma is only read by the core assembly above, so it can be overwritten here
-  BK_TRY(launch_sort_output(so, pr.jt, pr.t, s));
+  PHASE(PH_SORT, launch_sort_output(so, pr.jt, pr.t, s));
   // U' = [U Q] V[:, :r_new]
   GemmArgs g = gemm_base();
   g.M = d;
@@ -460,8 +465,8 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   g.round_bf16 = pr.bf16;
   g.C = at<void>(ws, p.o_Un);
   g.ldc = p.ldq;
-  BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
-  BK_TRY(launch_finalize(f->U, f->ldu, g.C, p.ldq, d, p.r_new, f->r, pr.t, s));
+  PHASE(PH_ROTATE, gemm_run(g, pr.t, pr.acc, pr.t, s));
+  PHASE(PH_FINALIZE, launch_finalize(f->U, f->ldu, g.C, p.ldq, d, p.r_new, f->r, pr.t, s));
   return BKFAC_OK;
 }
 
@@ -571,6 +576,7 @@ int bkfac_reorth(bkfac_factor* f, void* ws, size_t ws_bytes, bkfac_stream_t stre
   if (!jacobi_fits(p.C, p.b, p.rows_pad, p.pr.jt)) return BKFAC_EINVAL;
   const Prec& pr = p.pr;
   const int d = f->d;
+  TraceScope _reorth_ts(PH_REORTH, s);
   double* Gm = at<double>(ws, cap.o_G);
   double* R = at<double>(ws, cap.o_R);
   void* Rinv = at<void>(ws, cap.o_Rinv);
@@ -660,7 +666,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
   ca.cA_over = cAo;
   ca.cG_over = cGo;
   ca.alpha = alpha;
-  BK_TRY(launch_apply_coefs(ca, s));
+  PHASE(PH_COEFS, launch_apply_coefs(ca, s));
   // pass 1: T1 = G U_A (d_out x kA), T2 = diag(C_G / lamA') U_G^T G (kG x d_in, row-major)
   if (kA > 0) {
     GemmArgs g = gemm_base();
@@ -676,7 +682,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.round_bf16 = pr.bf16;
     g.C = T1;
     g.ldc = cap.ld1;
-    BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+    PHASE(PH_APPLY1, gemm_run(g, pr.t, pr.acc, pr.t, s));
   }
   if (kG > 0) {
     GemmArgs g = gemm_base();
@@ -693,7 +699,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.C = T2;  // column-major d_in x kG == row-major kG x d_in
     g.ldc = cap.ld2;
     g.cs = cGo;
-    BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+    PHASE(PH_APPLY1, gemm_run(g, pr.t, pr.acc, pr.t, s));
   }
   // small: T3' = diag(C_G) (U_G^T T1) diag(C_A);  W1 = T1 diag(C_A / lamG') + U_G T3'
   if (kA > 0) {
@@ -714,7 +720,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
       g.cs = cA;
       g.splits = gemm_pick_splits(kG, kA, dG, 152);
       g.partial = at<void>(ws, cap.o_part);
-      BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+      PHASE(PH_APPLY_SMALL, gemm_run(g, pr.t, pr.acc, pr.t, s));
     }
     GemmArgs g = gemm_base();
     g.M = dG;
@@ -732,7 +738,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.ldd = cap.ld1;
     g.beta = 1.0;
     g.ds = cAo;
-    BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+    PHASE(PH_APPLY_SMALL, gemm_run(g, pr.t, pr.acc, pr.t, s));
   }
   // pass 2: S = alpha G + W1 U_A^T + U_G W2
   {
@@ -759,7 +765,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.ldd = ldg;
     g.beta_dev = alpha;
     g.beta = 1.0;
-    BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
+    PHASE(PH_APPLY2, gemm_run(g, pr.t, pr.acc, pr.t, s));
   }
   return BKFAC_OK;
 }

@@ -84,6 +84,7 @@ enum DType { DT_F64 = 0, DT_F32 = 1 };
 
 // launchers implemented in gemm.cu; return a cudaError_t
 // in_t: element type of A/B; acc_t: accumulator; out_t: C/D element type
+// (the number of kernels launched is added to the launch counter)
 int gemm_run(const GemmArgs& g, DType in_t, DType acc_t, DType out_t, cudaStream_t s);
 // suggested split count for a long-K product with small output
 int gemm_pick_splits(int M, int N, int K, int sm_count);
@@ -190,5 +191,24 @@ struct ApplyCoefArgs {
   double* alpha;     // 1: 1 / (lamA' lamG')
 };
 int launch_apply_coefs(const ApplyCoefArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Tracing (trace.cu): per-phase CUDA-event timing and a launch counter
+// ---------------------------------------------------------------------------
+enum Phase {
+  PH_COLNORM, PH_PROJ, PH_RESID, PH_GRAM, PH_CHOL, PH_TRINV, PH_TRMM, PH_CORE, PH_JACOBI, PH_SORT,
+  PH_ROTATE, PH_FINALIZE, PH_DENSE, PH_COEFS, PH_APPLY1, PH_APPLY_SMALL, PH_APPLY2, PH_REORTH, PH_COUNT
+};
+class TraceScope {
+ public:
+  TraceScope(int ph, cudaStream_t s);
+  ~TraceScope();
+
+ private:
+  int ph_;
+  cudaStream_t s_;
+  void* a_;
+};
+void note_launches(int n);
 
 }  // namespace bkfac

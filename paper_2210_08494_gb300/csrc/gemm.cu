@@ -193,10 +193,12 @@ int run_typed(const GemmArgs& g, cudaStream_t s) {
     gemm_kernel<TIn, Acc, TOut, false, true><<<grid, NT, 0, s>>>(a);
   else
     gemm_kernel<TIn, Acc, TOut, false, false><<<grid, NT, 0, s>>>(a);
+  note_launches(1);
   if (a.splits > 1) {
     int64_t total = (int64_t)a.M * a.N;
     int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
     splitk_reduce<Acc, TOut><<<blocks, 256, 0, s>>>(a);
+    note_launches(1);
   }
   return (int)cudaGetLastError();
 }

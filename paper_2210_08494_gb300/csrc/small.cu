@@ -324,12 +324,14 @@ int launch_colnorm_max(const void* X, int64_t ldx, int d, int n, DType t, double
     colnorm_max_kernel<double><<<n, 256, 0, s>>>((const double*)X, ldx, d, out);
   else
     colnorm_max_kernel<float><<<n, 256, 0, s>>>((const float*)X, ldx, d, out);
+  note_launches(1);
   return (int)cudaGetLastError();
 }
 
 int launch_chol(const double* Gm, int n, double* R, double thr_rel, const double* scale, cudaStream_t s) {
   if (n <= 0) return 0;
   chol_kernel<<<1, 1024, 0, s>>>(Gm, n, R, thr_rel, scale);
+  note_launches(1);
   return (int)cudaGetLastError();
 }
 
@@ -340,6 +342,7 @@ int launch_trinv(const double* R, int n, void* Rinv, DType t, cudaStream_t s) {
     trinv_kernel<double><<<blocks, 1024, 0, s>>>(R, n, (double*)Rinv);
   else
     trinv_kernel<float><<<blocks, 1024, 0, s>>>(R, n, (float*)Rinv);
+  note_launches(1);
   return (int)cudaGetLastError();
 }
 
@@ -352,6 +355,7 @@ int launch_assemble_core(const CoreArgs& a, DType m_t, DType j_t, cudaStream_t s
     assemble_core_kernel<float, double><<<a.cols_pad, 256, 0, s>>>(a);
   else
     assemble_core_kernel<double, float><<<a.cols_pad, 256, 0, s>>>(a);
+  note_launches(1);
   return (int)cudaGetLastError();
 }
 
@@ -364,6 +368,7 @@ int launch_assemble_dense(const DenseArgs& a, DType u_t, DType j_t, cudaStream_t
     assemble_dense_kernel<float, double><<<a.cols_pad, 256, 0, s>>>(a);
   else
     assemble_dense_kernel<double, float><<<a.cols_pad, 256, 0, s>>>(a);
+  note_launches(1);
   return (int)cudaGetLastError();
 }
 
@@ -373,6 +378,7 @@ int launch_assemble_reorth(const double* R, const double* sigma, int k, int rows
     assemble_reorth_kernel<double><<<cols_pad, 256, 0, s>>>(R, sigma, k, rows_pad, (double*)L, colnorm2);
   else
     assemble_reorth_kernel<float><<<cols_pad, 256, 0, s>>>(R, sigma, k, rows_pad, (float*)L, colnorm2);
+  note_launches(1);
   return (int)cudaGetLastError();
 }
 
@@ -392,6 +398,7 @@ int launch_sort_output(const SortArgs& a, DType j_t, DType out_t, cudaStream_t s
     cudaFuncSetAttribute(sort_output_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     sort_output_kernel<float, double><<<1, 1024, smem, s>>>(a);
   }
+  note_launches(1);
   return (int)cudaGetLastError();
 }
 
@@ -403,11 +410,13 @@ int launch_finalize(void* U, int64_t ldu, const void* Unew, int64_t ldn, int d, 
     finalize_kernel<double><<<blocks, 256, 0, s>>>((double*)U, ldu, (const double*)Unew, ldn, d, r_new, r);
   else
     finalize_kernel<float><<<blocks, 256, 0, s>>>((float*)U, ldu, (const float*)Unew, ldn, d, r_new, r);
+  note_launches(1);
   return (int)cudaGetLastError();
 }
 
 int launch_apply_coefs(const ApplyCoefArgs& a, cudaStream_t s) {
   apply_coefs_kernel<<<1, 256, 0, s>>>(a);
+  note_launches(1);
   return (int)cudaGetLastError();
 }
 

@@ -53,7 +53,7 @@ def test_apply_ragged_shapes(oracle, dtype):
     print(f"apply dtype {dtype}: {err:.2e}")
 
 
-def test_apply_config1_f64(oracle):
+def test_apply_small_layer_f64(oracle):
     run_apply(oracle, 512, 64, 64, 256, 64, 64, bkfac.F64, lamA=0.1, lamG=0.1)
 
 
@@ -71,7 +71,7 @@ def test_apply_partial_ranks(oracle, kA, kG):
     run_apply(oracle, 100, 9, kA, 60, 7, kG, bkfac.F64)
 
 
-def test_apply_config2_full_size(oracle):
-    """Config-2 shape: G 4096 x 4097 FP32 with r_A = r_G = 256, lambda = 1e-2."""
+def test_apply_wide_layer_full_size(oracle):
+    """One wide FC layer: G 4096 x 4097 FP32 with r_A = r_G = 256, lambda = 1e-2."""
     err = run_apply(oracle, 4097, 256, 256, 4096, 256, 256, bkfac.F32, lamA=1e-2, lamG=1e-2)
-    print(f"config-2 apply relative error {err:.2e}")
+    print(f"wide-layer apply relative error {err:.2e}")

@@ -121,8 +121,8 @@ def test_init_keeps_rank_n_when_n_below_r(oracle):
     assert f.r_cur == 30
 
 
-def test_trajectory_f64_config1(oracle):
-    """Config-1 shape (d=512, r=64, n=32, rho=0.95, alpha=1.5), free-running for
+def test_trajectory_f64_small_factor(oracle):
+    """Small FP64 factor (d=512, r=64, n=32, rho=0.95, alpha=1.5), free-running for
     20 steps on both sides."""
     d, r, n, rho = 512, 64, 32, 0.95
     f = bkfac.Factor(d, r, bkfac.F64)
@@ -221,8 +221,8 @@ def test_invalid_arguments_are_rejected_before_launch():
     assert bkfac.bkfac_status() == bkfac.OK
 
 
-def test_config2_full_size_one_step(oracle):
-    """Config-2 shape (A factor: d = 4097, r = n = 256, FP32, rho = 0.95, alpha =
+def test_wide_layer_full_size_one_step(oracle):
+    """One wide FC layer's A factor (d = 4097, r = n = 256, FP32, rho = 0.95, alpha =
     1.2), in the launch configuration the benchmark times: init on the GPU,
     then one update compared with the oracle started from the GPU state."""
     d, r, n, rho = 4097, 256, 256, 0.95
@@ -237,6 +237,6 @@ def test_config2_full_size_one_step(oracle):
     Uo, so, info = oracle.update(Ug, sg, Ug.shape[0], rounded(X, f), rho, r)
     U2, s2 = gpu_state(f)
     es, er = rel(s2, so), lowrank_rel_err(U2, s2, Uo, so)
-    print(f"config-2 one-step: sigma {es:.2e} reconstruction {er:.2e} orth {orth_err(U2):.2e}")
+    print(f"wide-layer one-step: sigma {es:.2e} reconstruction {er:.2e} orth {orth_err(U2):.2e}")
     assert es < 1e-4 and er < 1e-4
     assert orth_err(U2) < 1e-4
