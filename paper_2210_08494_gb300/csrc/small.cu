@@ -228,10 +228,12 @@ __global__ void __launch_bounds__(1024) sort_output_kernel(const SortArgs a) {
   __shared__ double s_tiny;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const J* W = (const J*)a.W;
-  if (threadIdx.x == 0) {
+  if (wid == 0) {
+    // deterministic: fixed lane assignment, fixed shuffle tree
     double f = 0.0;
-    for (int j = 0; j < a.cols_pad; ++j) f += a.colnorm2[j];
-    s_tiny = 16.0 * Eps<J>::u * Eps<J>::u * f;
+    for (int j = lane; j < a.cols_pad; j += 32) f += a.colnorm2[j];
+    f = warp_sum(f);
+    if (lane == 0) s_tiny = 16.0 * Eps<J>::u * Eps<J>::u * f;
   }
   for (int i = wid; i < a.cols; i += nw) {
     const J* w = W + (int64_t)i * a.rows_pad;
