@@ -183,6 +183,27 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
                 int64_t ldg, void* S, int64_t lds, uint32_t flags, void* ws, size_t ws_bytes,
                 bkfac_stream_t stream);
 
+/* The damped inverse application without a caller workspace.  There is no
+ * counterpart in the paper: this is an interface for callers that cannot
+ * allocate device memory (code running under a stream capture that forbids
+ * synchronising calls, frameworks whose device memory belongs to their own
+ * pool allocator, latency-critical loops that cannot afford cudaMalloc's
+ * implicit synchronisation).  Same arguments and result as bkfac_apply; the
+ * workspace is a fixed array of BKFAC_NOALLOC_SCRATCH_BYTES that the library
+ * keeps on every device that loads it, until the process exits.
+ *   - Returns BKFAC_EWORKSPACE, before enqueuing anything, when the factor
+ *     pair needs more than BKFAC_NOALLOC_SCRATCH_BYTES
+ *     (bkfac_apply_workspace_size(fA, fG) tells how much it needs).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls on a device share the one array: calls that may overlap on
+ *     the GPU (different streams without ordering) race on it and give
+ *     undefined results.  Order them on one stream or with events.
+ *   - Allocates nothing: no cudaMalloc / cudaFree, no allocating library call. */
+#define BKFAC_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int bkfac_apply_noalloc(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, double lamG, const void* G,
+                        int64_t ldg, void* S, int64_t lds, uint32_t flags, bkfac_stream_t stream);
+
 /* Diagnostics for tests: byte offsets, inside an update workspace, of the
  * intermediates left by the last bkfac_init / bkfac_update that used it:
  *   out[0] M (r_cur_old x n, column-major, dtype of U)

@@ -78,6 +78,7 @@ def load(build_if_missing: bool = True):
             "bkfac_update": ([FP, P, I64, I, D, P, S, P], I),
             "bkfac_reorth": ([FP, P, S, P], I),
             "bkfac_apply": ([FP, FP, D, D, P, I64, P, I64, U32, P, S, P], I),
+            "bkfac_apply_noalloc": ([FP, FP, D, D, P, I64, P, I64, U32, P], I),
             "bkfac_debug_offsets": ([FP, I, ctypes.POINTER(ctypes.c_int64)], I),
             "bkfac_batch_create": ([ctypes.POINTER(bkfac_layer_desc), I, I, I, ctypes.c_char_p], P),
             "bkfac_batch_get_factor": ([P, I, I, FP], I),
@@ -112,7 +113,7 @@ def exported_symbols():
               "bkfac_apply_workspace_size", "bkfac_init", "bkfac_update", "bkfac_reorth", "bkfac_apply",
               "bkfac_debug_offsets", "bkfac_batch_create", "bkfac_batch_get_factor", "bkfac_batch_update",
               "bkfac_batch_apply", "bkfac_batch_step_graph", "bkfac_batch_destroy", "bkfac_trace_enable",
-              "bkfac_trace_read", "bkfac_trace_phase_name"):
+              "bkfac_trace_read", "bkfac_trace_phase_name", "bkfac_apply_noalloc"):
         if hasattr(lib, n):
             names.append(n)
     return names
@@ -299,3 +300,4 @@ def bkfac_trace_read():
 
 def bkfac_launch_count() -> int:
     return bkfac_trace_read()[1]
+
