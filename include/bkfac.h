@@ -231,6 +231,17 @@ int bkfac_trace_enable(int on);
 int bkfac_trace_read(double* ms, int64_t* count, int nmax, int64_t* launches);
 const char* bkfac_trace_phase_name(int id);
 
+/* ---- autotuning -------------------------------------------------------------
+ * Times the candidate launch shapes of factor f's eigensolve at batch width n
+ * (block width of the Jacobi blocks, hence the cluster size, and the exchange
+ * of the blocks between rounds: through L2 or over distributed shared memory)
+ * on a synthetic core of that shape, on the current device, and records the
+ * fastest in a process-wide table that later calls use.  cache_path (may be
+ * NULL): a text file read before and written after tuning.  Allocates
+ * temporary device memory; call it outside any stream capture.  The choice
+ * only changes launch shapes, never the decomposition computed. */
+int bkfac_tune(const bkfac_factor* f, int n, const char* cache_path);
+
 /* ---- batched calls: all factors of all FC layers -------------------------
  * A batch groups the two factors of nlayers layers (uneven d, r) with a
  * common batch width n and dtype.  Each phase of the update and of the apply

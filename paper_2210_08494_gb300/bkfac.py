@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
                                         ctypes.POINTER(D), U32, I, P], I),
             "bkfac_batch_destroy": ([P], None),
             "bkfac_trace_enable": ([I], I),
+            "bkfac_tune": ([FP, I, ctypes.c_char_p], I),
             "bkfac_trace_read": ([ctypes.POINTER(D), ctypes.POINTER(I64), I, ctypes.POINTER(I64)], I),
             "bkfac_trace_phase_name": ([I], ctypes.c_char_p),
         }
@@ -113,7 +114,7 @@ def exported_symbols():
               "bkfac_apply_workspace_size", "bkfac_init", "bkfac_update", "bkfac_reorth", "bkfac_apply",
               "bkfac_debug_offsets", "bkfac_batch_create", "bkfac_batch_get_factor", "bkfac_batch_update",
               "bkfac_batch_apply", "bkfac_batch_step_graph", "bkfac_batch_destroy", "bkfac_trace_enable",
-              "bkfac_trace_read", "bkfac_trace_phase_name", "bkfac_apply_noalloc"):
+              "bkfac_trace_read", "bkfac_trace_phase_name", "bkfac_apply_noalloc", "bkfac_tune"):
         if hasattr(lib, n):
             names.append(n)
     return names
@@ -301,3 +302,90 @@ def bkfac_trace_read():
 def bkfac_launch_count() -> int:
     return bkfac_trace_read()[1]
 
+
+# --------------------------------------------------------------------------- batch
+
+
+def _arr(ctype, vals):
+    return (ctype * len(vals))(*vals)
+
+
+class Batch:
+    """All factors of all FC layers (bkfac_batch_*): grouped update / apply and
+    one-graph replay of a full step.  layers: list of (Factor A, Factor G); the
+    batch works on copies of their descriptors and owns its own workspace."""
+
+    def __init__(self, layers, n: int, dtype: int = F32, tune_cache: str | None = None):
+        self.layers = layers
+        self.n = int(n)
+        self.dtype = int(dtype)
+        descs = (bkfac_layer_desc * len(layers))(*[bkfac_layer_desc(a.desc, g.desc) for a, g in layers])
+        h = load().bkfac_batch_create(descs, len(layers), self.n, self.dtype,
+                                      tune_cache.encode() if tune_cache else None)
+        if not h:
+            raise BkfacError(EINVAL, "bkfac_batch_create")
+        self.h = ctypes.c_void_p(h)
+        self._graph_args = None
+
+    def factor(self, layer: int, which: int) -> bkfac_factor:
+        out = bkfac_factor()
+        _check(load().bkfac_batch_get_factor(self.h, layer, which, ctypes.byref(out)), "bkfac_batch_get_factor")
+        return out
+
+    def sync_descriptors(self):
+        """Copy the batch's r_cur / step back into the layers' Factor objects."""
+        for l, (a, g) in enumerate(self.layers):
+            for w, f in ((0, a), (1, g)):
+                d = self.factor(l, w)
+                f.desc.r_cur, f.desc.step = d.r_cur, d.step
+
+    def update(self, XA, XG, rho: float, stream=None):
+        P = ctypes.c_void_p
+        _check(load().bkfac_batch_update(self.h, _arr(P, [x.data_ptr() for x in XA]),
+                                         _arr(ctypes.c_int64, [_cols_ld(x) for x in XA]),
+                                         _arr(P, [x.data_ptr() for x in XG]),
+                                         _arr(ctypes.c_int64, [_cols_ld(x) for x in XG]), float(rho),
+                                         _stream(stream)), "bkfac_batch_update")
+
+    def apply(self, G, S, lamA, lamG, flags: int = 0, stream=None):
+        P = ctypes.c_void_p
+        _check(load().bkfac_batch_apply(self.h, _arr(P, [g.data_ptr() for g in G]),
+                                        _arr(ctypes.c_int64, [g.stride(0) for g in G]),
+                                        _arr(P, [s.data_ptr() for s in S]),
+                                        _arr(ctypes.c_int64, [s.stride(0) for s in S]),
+                                        _arr(ctypes.c_double, list(lamA)), _arr(ctypes.c_double, list(lamG)),
+                                        int(flags), _stream(stream)), "bkfac_batch_apply")
+
+    def step_graph(self, XA=None, XG=None, rho=0.95, G=None, S=None, lamA=None, lamG=None, flags: int = 0,
+                   capture: bool = False, stream=None):
+        """capture=True: capture one full step (update then apply) with these
+        tensors and replay it once; capture=False: replay the captured graph."""
+        P = ctypes.c_void_p
+        lib = load()
+        if capture:
+            args = (_arr(P, [x.data_ptr() for x in XA]), _arr(ctypes.c_int64, [_cols_ld(x) for x in XA]),
+                    _arr(P, [x.data_ptr() for x in XG]), _arr(ctypes.c_int64, [_cols_ld(x) for x in XG]),
+                    float(rho), _arr(P, [g.data_ptr() for g in G]), _arr(ctypes.c_int64, [g.stride(0) for g in G]),
+                    _arr(P, [s.data_ptr() for s in S]), _arr(ctypes.c_int64, [s.stride(0) for s in S]),
+                    _arr(ctypes.c_double, list(lamA)), _arr(ctypes.c_double, list(lamG)))
+            self._graph_args = args
+            _check(lib.bkfac_batch_step_graph(self.h, *args, int(flags), 1, _stream(stream)), "bkfac_batch_step_graph")
+        else:
+            _check(lib.bkfac_batch_step_graph(self.h, None, None, None, None, 0.0, None, None, None, None, None,
+                                              None, int(flags), 0, _stream(stream)), "bkfac_batch_step_graph")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().bkfac_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bkfac_tune(f: Factor, n: int, cache_path: str | None = None):
+    """Autotune the eigensolve launch shape of f at batch width n (see include/bkfac.h)."""
+    _check(load().bkfac_tune(ctypes.byref(f.desc), int(n), cache_path.encode() if cache_path else None), "bkfac_tune")

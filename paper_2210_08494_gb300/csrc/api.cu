@@ -78,7 +78,8 @@ struct UpdatePlan {
   int64_t ldq, ldm, ldv;
   int C, b, rows_pad, cols_pad;  // Jacobi plan of this call
   int rows_cap, cols_cap;        // capacity of L
-  size_t o_scale, o_M, o_part, o_P, o_Q1, o_Q, o_G, o_R1, o_R2, o_Rinv, o_L, o_cn, o_lam, o_V, o_Un, o_sw;
+  size_t o_scale, o_M, o_part, o_P, o_Q1, o_Q, o_G, o_R1, o_R2, o_Rinv, o_L, o_cn, o_lam, o_V, o_Un, o_sw, o_st;
+  size_t part_bytes;
   size_t total;
 };
 
@@ -112,7 +113,8 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
     p.o_L = L.add((size_t)rows_cap * cols_cap * jes);
     p.o_cn = L.add((size_t)cols_cap * 8);
     p.o_lam = L.add((size_t)cols_cap * 8);
-    p.o_sw = L.add(16);
+    p.o_sw = L.add(256);
+    p.o_st = L.add((size_t)cols_cap * 4);
   } else {
     const int kmax = f->r, Nmax = f->r + n;
     p.N = k + n;
@@ -128,6 +130,7 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
     p.o_M = L.add((size_t)p.ldm * n * es);
     const size_t part = std::max(partial_bytes(kmax, n, f->d, aes), partial_bytes(n, n, f->d, 8));
     p.o_part = L.add(part);
+    p.part_bytes = part;
     p.o_P = L.add((size_t)p.ldq * n * es);
     p.o_Q1 = L.add((size_t)p.ldq * n * es);
     p.o_Q = L.add((size_t)p.ldq * n * es);
@@ -140,7 +143,8 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
     p.o_lam = L.add((size_t)cols_cap * 8);
     p.o_V = L.add((size_t)p.ldv * f->r * es);
     p.o_Un = L.add((size_t)p.ldq * f->r * es);
-    p.o_sw = L.add(16);
+    p.o_sw = L.add(256);
+    p.o_st = L.add((size_t)cols_cap * 4);
   }
   p.rows_cap = rows_cap;
   p.cols_cap = cols_cap;
@@ -154,7 +158,7 @@ struct ReorthPlan {
   Prec pr;
   int64_t ldq, ldv;
   int C, b, rows_pad, cols_pad, rows_cap, cols_cap;
-  size_t o_part, o_G, o_R, o_Rinv, o_Q, o_L, o_cn, o_lam, o_V, o_Un, o_sw, total;
+  size_t o_part, o_G, o_R, o_Rinv, o_Q, o_L, o_cn, o_lam, o_V, o_Un, o_sw, o_st, total;
 };
 
 ReorthPlan plan_reorth(const bkfac_factor* f, int k) {
@@ -182,7 +186,8 @@ ReorthPlan plan_reorth(const bkfac_factor* f, int k) {
   p.o_lam = L.add((size_t)p.cols_cap * 8);
   p.o_V = L.add((size_t)p.ldv * kmax * es);
   p.o_Un = L.add((size_t)p.ldq * kmax * es);
-  p.o_sw = L.add(16);
+  p.o_sw = L.add(256);
+  p.o_st = L.add((size_t)p.cols_cap * 4);
   p.total = L.total;
   return p;
 }
@@ -192,7 +197,8 @@ struct ApplyPlan {
   int dA, dG, kA, kG;
   Prec pr;
   int64_t ld1, ld2, ldw;
-  size_t o_T1, o_T2, o_T3, o_W1, o_part, o_cA, o_cG, o_cAo, o_cGo, o_alpha, total;
+  size_t o_T1, o_T2, o_T3, o_W1, o_part, o_part1, o_cA, o_cG, o_cAo, o_cGo, o_alpha, total;
+  size_t part1_bytes;
 };
 
 ApplyPlan plan_apply(const bkfac_factor* fA, const bkfac_factor* fG, int kA, int kG) {
@@ -213,6 +219,9 @@ ApplyPlan plan_apply(const bkfac_factor* fA, const bkfac_factor* fG, int kA, int
   p.o_T2 = L.add((size_t)p.ld2 * rG * es);
   p.o_T3 = L.add((size_t)p.ldw * rA * es);
   p.o_part = L.add(partial_bytes(rG, rA, p.dG, aes));
+  // pass 1 may split K in two: scratch for two copies of the larger of T1 / T2
+  p.part1_bytes = (size_t)2 * std::max((size_t)p.dG * rA, (size_t)p.dA * rG) * aes;
+  p.o_part1 = L.add(p.part1_bytes);
   p.o_cA = L.add((size_t)rA * 8);
   p.o_cG = L.add((size_t)rG * 8);
   p.o_cAo = L.add((size_t)rA * 8);
@@ -240,6 +249,16 @@ P* at(void* ws, size_t off) {
     BK_TRY(expr);                        \
   } while (0)
 
+// Cholesky: the cluster kernel when n fits it, else the single-CTA kernel
+int run_chol(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
+             cudaStream_t s) {
+  if (chol_cluster_size(n) > 0) return launch_chol_cluster(Gm, n, R, thr_rel, scale, near_tol, s);
+  return launch_chol(Gm, n, R, thr_rel, scale, s);
+}
+
+// second CholeskyQR pass: G2 = I + E; the near-identity factor's error is O(|E|^2)
+double near_identity_tol(const Prec& pr) { return pr.t == DT_F64 ? 1e-9 : 1e-5; }
+
 GemmArgs gemm_base() {
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
@@ -263,14 +282,17 @@ int run_gram(const void* A, int64_t lda, int d, int n, Prec pr, double* G, void*
   g.b_kmaj = true;
   g.C = G;
   g.ldc = n;
-  g.splits = gemm_pick_splits(n, n, d, 152);
+  g.sym = true;
+  g.splits = std::max(2, gemm_pick_splits(n, n, d, 152));
   g.partial = part;
+  // FP32 data: FP64-accurate Gram on the FP32 pipes (compensated); FP64 data: DFMA
+  if (pr.t == DT_F32) return gram_run_comp(g, s);
   return gemm_run(g, pr.t, DT_F64, DT_F64, s);
 }
 
 // Q = P Rinv (d x n times n x n upper), output column-major ld ldq
 int run_trmm(const void* P, int64_t ldp, int d, int n, const void* Rinv, Prec pr, void* Q, int64_t ldq,
-             cudaStream_t s) {
+             void* part, size_t part_bytes, cudaStream_t s) {
   GemmArgs g = gemm_base();
   g.M = d;
   g.N = n;
@@ -283,6 +305,8 @@ int run_trmm(const void* P, int64_t ldp, int d, int n, const void* Rinv, Prec pr
   g.b_kmaj = true;
   g.C = Q;
   g.ldc = ldq;
+  g.partial = part;
+  g.partial_bytes = part_bytes;
   return gemm_run(g, pr.t, pr.acc, pr.t, s);
 }
 
@@ -312,11 +336,13 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     JacobiProblem jp;
     jp.W = a.F;
     jp.rows = d;
+    jp.cols = k + n;
     jp.rows_pad = p.rows_pad;
     jp.cols_pad = p.cols_pad;
     jp.b = p.b;
     jp.colnorm2 = a.colnorm2;
     jp.sweeps_out = at<int>(ws, p.o_sw);
+    jp.stamp = at<int>(ws, p.o_st);
     PHASE(PH_JACOBI, launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(d, pr.jt), kMaxSweeps, s));
     SortArgs so;
     so.W = a.F;
@@ -389,6 +415,8 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     h.ldd = ldx;
     h.alpha = -1.0;
     h.beta = 1.0;
+    h.partial = part;
+    h.partial_bytes = p.part_bytes;
     PHASE(PH_RESID, gemm_run(h, pr.t, pr.acc, pr.t, s));
     Pp = P;
     ldp = p.ldq;
@@ -398,13 +426,13 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   const double thr1 = pr.bf16 ? (2.0 * ue) * (2.0 * ue) : (64.0 * ue) * (64.0 * ue);
   const double thr2 = (64.0 * pr.u_t) * (64.0 * pr.u_t);
   PHASE(PH_GRAM, run_gram(Pp, ldp, d, n, pr, Gm, part, s));
-  PHASE(PH_CHOL, launch_chol(Gm, n, R1, thr1, scale, s));
+  PHASE(PH_CHOL, run_chol(Gm, n, R1, thr1, scale, 0.0, s));
   PHASE(PH_TRINV, launch_trinv(R1, n, Rinv, pr.t, s));
-  PHASE(PH_TRMM, run_trmm(Pp, ldp, d, n, Rinv, pr, Q1, p.ldq, s));
+  PHASE(PH_TRMM, run_trmm(Pp, ldp, d, n, Rinv, pr, Q1, p.ldq, part, p.part_bytes, s));
   PHASE(PH_GRAM, run_gram(Q1, p.ldq, d, n, pr, Gm, part, s));
-  PHASE(PH_CHOL, launch_chol(Gm, n, R2, thr2, nullptr, s));
+  PHASE(PH_CHOL, run_chol(Gm, n, R2, thr2, nullptr, near_identity_tol(pr), s));
   PHASE(PH_TRINV, launch_trinv(R2, n, Rinv, pr.t, s));
-  PHASE(PH_TRMM, run_trmm(Q1, p.ldq, d, n, Rinv, pr, Q, p.ldq, s));
+  PHASE(PH_TRMM, run_trmm(Q1, p.ldq, d, n, Rinv, pr, Q, p.ldq, part, p.part_bytes, s));
   // core factor L and its Jacobi eigensolve
   CoreArgs ca;
   ca.k = k;
@@ -425,11 +453,13 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   JacobiProblem jp;
   jp.W = ca.L;
   jp.rows = p.N;
+  jp.cols = p.N;
   jp.rows_pad = p.rows_pad;
   jp.cols_pad = p.cols_pad;
   jp.b = p.b;
   jp.colnorm2 = ca.colnorm2;
   jp.sweeps_out = at<int>(ws, p.o_sw);
+  jp.stamp = at<int>(ws, p.o_st);
   PHASE(PH_JACOBI, launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(p.N, pr.jt), kMaxSweeps, s));
   SortArgs so;
   so.W = ca.L;
@@ -465,6 +495,8 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   g.round_bf16 = pr.bf16;
   g.C = at<void>(ws, p.o_Un);
   g.ldc = p.ldq;
+  g.partial = part;
+  g.partial_bytes = p.part_bytes;
   PHASE(PH_ROTATE, gemm_run(g, pr.t, pr.acc, pr.t, s));
   PHASE(PH_FINALIZE, launch_finalize(f->U, f->ldu, g.C, p.ldq, d, p.r_new, f->r, pr.t, s));
   return BKFAC_OK;
@@ -478,7 +510,7 @@ int check_ws(void* ws, size_t ws_bytes, size_t need) {
 
 bool jacobi_fits(int C, int b, int rows_pad, DType jt) {
   (void)C;
-  return jacobi_smem_bytes(b, rows_pad, jt) <= 227 * 1024;
+  return jacobi_smem_bytes(b, rows_pad, jt) <= 200 * 1024;
 }
 
 int update_common(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, void* ws, size_t ws_bytes,
@@ -582,20 +614,22 @@ int bkfac_reorth(bkfac_factor* f, void* ws, size_t ws_bytes, bkfac_stream_t stre
   void* Rinv = at<void>(ws, cap.o_Rinv);
   void* Q = at<void>(ws, cap.o_Q);
   BK_TRY(run_gram(f->U, f->ldu, d, k, pr, Gm, at<void>(ws, cap.o_part), s));
-  BK_TRY(launch_chol(Gm, k, R, (64.0 * pr.u_t) * (64.0 * pr.u_t), nullptr, s));
+  BK_TRY(run_chol(Gm, k, R, (64.0 * pr.u_t) * (64.0 * pr.u_t), nullptr, 0.0, s));
   BK_TRY(launch_trinv(R, k, Rinv, pr.t, s));
-  BK_TRY(run_trmm(f->U, f->ldu, d, k, Rinv, pr, Q, cap.ldq, s));
+  BK_TRY(run_trmm(f->U, f->ldu, d, k, Rinv, pr, Q, cap.ldq, nullptr, 0, s));
   void* Lm = at<void>(ws, cap.o_L);
   double* cn = at<double>(ws, cap.o_cn);
   BK_TRY(launch_assemble_reorth(R, f->sigma, k, p.rows_pad, p.cols_pad, Lm, cn, pr.jt, s));
   JacobiProblem jp;
   jp.W = Lm;
   jp.rows = k;
+  jp.cols = k;
   jp.rows_pad = p.rows_pad;
   jp.cols_pad = p.cols_pad;
   jp.b = p.b;
   jp.colnorm2 = cn;
   jp.sweeps_out = at<int>(ws, cap.o_sw);
+  jp.stamp = at<int>(ws, cap.o_st);
   BK_TRY(launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(k, pr.jt), kMaxSweeps, s));
   SortArgs so;
   so.W = Lm;
@@ -682,6 +716,8 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.round_bf16 = pr.bf16;
     g.C = T1;
     g.ldc = cap.ld1;
+    g.partial = at<void>(ws, cap.o_part1);
+    g.partial_bytes = cap.part1_bytes;
     PHASE(PH_APPLY1, gemm_run(g, pr.t, pr.acc, pr.t, s));
   }
   if (kG > 0) {
@@ -699,6 +735,8 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.C = T2;  // column-major d_in x kG == row-major kG x d_in
     g.ldc = cap.ld2;
     g.cs = cGo;
+    g.partial = at<void>(ws, cap.o_part1);
+    g.partial_bytes = cap.part1_bytes;
     PHASE(PH_APPLY1, gemm_run(g, pr.t, pr.acc, pr.t, s));
   }
   // small: T3' = diag(C_G) (U_G^T T1) diag(C_A);  W1 = T1 diag(C_A / lamG') + U_G T3'

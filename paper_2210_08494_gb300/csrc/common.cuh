@@ -66,6 +66,7 @@ struct GemmArgs {
   const void* B1;
   int64_t ldb1;
   bool a_kmaj, b_kmaj, c_rowmaj, round_bf16;
+  bool sym;        // C = A^T A with M == N and B == A: only upper tiles are computed
   void* C;
   int64_t ldc;
   const void* D;
@@ -78,6 +79,7 @@ struct GemmArgs {
   int splits;      // split-K count (1 = direct epilogue)
   int k_chunk;     // K elements per split (multiple of the tile depth)
   void* partial;   // splits * M * N accumulators when splits > 1
+  size_t partial_bytes;  // size of `partial` (bounds any split count the GEMM picks itself)
 };
 
 enum DType { DT_F64 = 0, DT_F32 = 1 };
@@ -86,6 +88,9 @@ enum DType { DT_F64 = 0, DT_F32 = 1 };
 // in_t: element type of A/B; acc_t: accumulator; out_t: C/D element type
 // (the number of kernels launched is added to the launch counter)
 int gemm_run(const GemmArgs& g, DType in_t, DType acc_t, DType out_t, cudaStream_t s);
+// Gram A^T A of FP32 data with compensated FP32 accumulation (FP64-level accuracy),
+// output FP64; uses g.A0/lda0 (K-major), g.M = g.N, g.K0, g.C/ldc, g.partial, g.splits
+int gram_run_comp(const GemmArgs& g, cudaStream_t s);
 // suggested split count for a long-K product with small output
 int gemm_pick_splits(int M, int N, int K, int sm_count);
 
@@ -97,6 +102,11 @@ int launch_colnorm_max(const void* X, int64_t ldx, int d, int n, DType t, double
 // thresholded Cholesky of an n x n FP64 Gram (column-major, ld n): upper R (n x n, ld n);
 // pivot j dropped (row j of R zero) when s_j <= thr_rel * (*scale).  scale may be null (= 1).
 int launch_chol(const double* Gm, int n, double* R, double thr_rel, const double* scale, cudaStream_t s);
+// the same factorisation on a thread-block cluster (chol.cu); with near_tol > 0 and
+// max|G - I| <= near_tol the factor is I + (strict upper part + half diagonal of G - I)
+int launch_chol_cluster(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
+                        cudaStream_t s);
+int chol_cluster_size(int n);  // 0 when n is too large for the cluster kernel
 // inverse of the upper-triangular R (zero rows = dropped pivots -> zero rows/cols of Rinv)
 int launch_trinv(const double* R, int n, void* Rinv, DType t, cudaStream_t s);
 
@@ -138,9 +148,10 @@ int launch_assemble_reorth(const double* R, const double* sigma, int k, int rows
 // ---------------------------------------------------------------------------
 struct JacobiProblem {
   void* W;
-  int rows, rows_pad, cols_pad, b;   // cols_pad = 2 * C * b
+  int rows, cols, rows_pad, cols_pad, b;   // cols_pad = 2 * C * b >= cols
   const double* colnorm2;            // cols_pad squared column norms of the input
-  int* sweeps_out;                   // optional
+  int* sweeps_out;                   // optional: [0] sweeps, [1 + s] rotations in sweep s (s < 48)
+  int* stamp;                        // cols_pad ints of scratch (last sweep a column rotated)
 };
 constexpr int kMaxJacobiProblems = 64;
 struct JacobiBatch {
@@ -150,6 +161,15 @@ struct JacobiBatch {
 // (passed by value as a kernel parameter, so the launch can be captured in a graph)
 int launch_jacobi(const JacobiProblem* probs, int nprob, int C, DType j_t, double tol, int max_sweeps,
                   cudaStream_t s);
+// explicit block-exchange mode (false: through L2, true: distributed shared memory)
+int launch_jacobi_mode(const JacobiProblem* probs, int nprob, int C, DType j_t, double tol, int max_sweeps,
+                       bool want_dsm, cudaStream_t s);
+void jacobi_plan_with(int rows, int cols, DType j_t, int b_max, int* C, int* b, int* rows_pad, int* cols_pad);
+// tuning table (tune.cu): tuned block width and exchange mode for a (rows, cols, precision)
+bool tune_lookup(int rows, int cols, DType jt, int* b, int* dsm);
+int tune_shape(int rows, int cols, DType jt);
+int tune_load(const char* path);
+int tune_save(const char* path);
 // shared memory bytes one CTA needs for a problem
 size_t jacobi_smem_bytes(int b, int rows_pad, DType j_t);
 // choose cluster size and block width for a problem
@@ -210,5 +230,6 @@ class TraceScope {
   void* a_;
 };
 void note_launches(int n);
+int64_t launch_count();
 
 }  // namespace bkfac

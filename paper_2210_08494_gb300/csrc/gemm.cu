@@ -64,18 +64,20 @@ __device__ __forceinline__ TIn load_b(const GemmArgs& g, int k, int n, bool rnd)
   return BKM ? load_in<TIn>(B + (int64_t)n * ldb + k, rnd) : load_in<TIn>(B + (int64_t)k * ldb + n, rnd);
 }
 
+// The epilogue computes in the accumulator's precision (FP32 for the FP32 paths:
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU).
 template <typename Acc, typename TOut>
 __device__ __forceinline__ void epilogue_store(const GemmArgs& g, int m, int n, Acc acc) {
-  double v = (double)acc * g.alpha;
-  if (g.rs) v *= g.rs[m];
-  if (g.cs) v *= g.cs[n];
-  double beta = g.beta_dev ? *g.beta_dev : g.beta;
-  int64_t off = g.c_rowmaj ? (int64_t)m * g.ldc + n : (int64_t)m + (int64_t)n * g.ldc;
+  Acc v = acc * (Acc)g.alpha;
+  if (g.rs) v *= (Acc)g.rs[m];
+  if (g.cs) v *= (Acc)g.cs[n];
+  const double beta = g.beta_dev ? *g.beta_dev : g.beta;
+  const int64_t off = g.c_rowmaj ? (int64_t)m * g.ldc + n : (int64_t)m + (int64_t)n * g.ldc;
   if (g.D != nullptr && beta != 0.0) {
-    int64_t doff = g.c_rowmaj ? (int64_t)m * g.ldd + n : (int64_t)m + (int64_t)n * g.ldd;
-    double dv = (double)((const TOut*)g.D)[doff];
-    if (g.ds) dv *= g.ds[n];
-    v += beta * dv;
+    const int64_t doff = g.c_rowmaj ? (int64_t)m * g.ldd + n : (int64_t)m + (int64_t)n * g.ldd;
+    Acc dv = (Acc)((const TOut*)g.D)[doff];
+    if (g.ds) dv *= (Acc)g.ds[n];
+    v += (Acc)beta * dv;
   }
   ((TOut*)g.C)[off] = (TOut)v;
 }
@@ -87,6 +89,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmArgs g) {
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  if (g.sym && blockIdx.y > blockIdx.x) return;  // symmetric product: upper tiles only
   const int K = g.K0 + g.K1;
   const int kb = blockIdx.z * g.k_chunk;
   const int ke = min(K, kb + g.k_chunk);
@@ -144,7 +147,10 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmArgs g) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
-        if (m < g.M && n < g.N) epilogue_store<Acc, TOut>(g, m, n, acc[i][j]);
+        if (m < g.M && n < g.N) {
+          epilogue_store<Acc, TOut>(g, m, n, acc[i][j]);
+          if (g.sym && blockIdx.y != blockIdx.x) epilogue_store<Acc, TOut>(g, n, m, acc[i][j]);
+        }
       }
   } else {
     Acc* P = (Acc*)g.partial + (int64_t)blockIdx.z * g.M * g.N;
@@ -158,17 +164,325 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmArgs g) {
   }
 }
 
+// Gram C = A^T A of an FP32 matrix with FP64-level accuracy on the FP32 pipes.
+// Each product is split exactly (p = a b rounded, e = fma(a, b, -p)) and the
+// rounded parts are summed with Knuth's TwoSum, whose rounding errors join the
+// product errors in a compensation term: s + c carries the dot product to
+// about u32^2 relative to sum |a_k b_k|.  The split partials are written as
+// double (s + c) and summed in FP64 by splitk_reduce.  Upper tiles only.
+struct Comp {
+  float s, c;
+};
+
+// explicit round-to-nearest intrinsics: the transformation is only error-free
+// if no step is contracted into an FMA or reassociated
+__device__ __forceinline__ void comp_fma(Comp& acc, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float t = __fadd_rn(acc.s, p);
+  const float z = __fsub_rn(t, acc.s);
+  const float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  acc.s = t;
+  acc.c = __fadd_rn(acc.c, __fadd_rn(err, e));
+}
+
+__global__ void __launch_bounds__(NT) gram_comp_kernel(const GemmArgs g) {
+  __shared__ float As[BKK][BM + 1];
+  __shared__ float Bs[BKK][BN + 1];
+  if (blockIdx.y > blockIdx.x) return;
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int K = g.K0;
+  const int kb = blockIdx.z * g.k_chunk;
+  const int ke = min(K, kb + g.k_chunk);
+  const float* A = (const float*)g.A0;
+  Comp acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = Comp{0.f, 0.f};
+  for (int kt = kb; kt < ke; kt += BKK) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + NT * q;
+      const int kk = e % BKK, mm = e / BKK;
+      const int k = kt + kk;
+      As[kk][mm] = (m0 + mm < g.M && k < ke) ? __ldg(A + (int64_t)(m0 + mm) * g.lda0 + k) : 0.f;
+      Bs[kk][mm] = (n0 + mm < g.N && k < ke) ? __ldg(A + (int64_t)(n0 + mm) * g.lda0 + k) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BKK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) comp_fma(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+  double* P = (double*)g.partial + (int64_t)blockIdx.z * g.M * g.N;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+      if (m < g.M && n < g.N) P[(int64_t)m * g.N + n] = (double)acc[i][j].s + (double)acc[i][j].c;
+    }
+}
+
 // sums the split partials in split order, then applies the epilogue
 template <typename Acc, typename TOut>
 __global__ void __launch_bounds__(256) splitk_reduce(const GemmArgs g) {
   const int64_t total = (int64_t)g.M * g.N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const Acc* P = (const Acc*)g.partial;
-    Acc s = Acc(0);
-    for (int z = 0; z < g.splits; ++z) s += P[(int64_t)z * total + e];
     const int m = (int)(e / g.N), n = (int)(e % g.N);
+    // symmetric product: only upper tiles were computed; lower entries mirror them
+    const int64_t src = (g.sym && (m / BM) > (n / BN)) ? (int64_t)n * g.N + m : e;
+    Acc s = Acc(0);
+    for (int z = 0; z < g.splits; ++z) s += P[(int64_t)z * total + src];
     epilogue_store<Acc, TOut>(g, m, n, s);
   }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 SIMT GEMM for the large products: 128 x 128 tiles, 8 x 8 outputs per
+// thread (four 4 x 4 quadrants at offsets 0 / 64 so shared-memory reads are
+// 16-byte and conflict-free), 16-byte global loads, two shared-memory stages
+// with the next tile prefetched into registers while the current one is used.
+// Requires 16-byte aligned operands with leading dimensions a multiple of 4
+// and a first K segment that is a multiple of the tile depth (checked by the
+// caller); edges are zero-filled.
+// ---------------------------------------------------------------------------
+constexpr int LBM = 128, LBN = 128, LBK = 8, LNT = 256;
+
+template <bool AK>
+__device__ __forceinline__ float4 ld_a4(const GemmArgs& g, int m, int k, int ke, bool rnd) {
+  // four consecutive elements along M (M-major) or along K (K-major)
+  const float* A;
+  int64_t lda;
+  int kk = k;
+  if (k < g.K0) {
+    A = (const float*)g.A0;
+    lda = g.lda0;
+  } else {
+    A = (const float*)g.A1;
+    lda = g.lda1;
+    kk = k - g.K0;
+  }
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (AK) {
+    if (m < g.M) {
+      const float* p = A + (int64_t)m * lda + kk;
+      if (k + 3 < ke) {
+        v = __ldg(reinterpret_cast<const float4*>(p));
+      } else {
+        if (k < ke) v.x = __ldg(p);
+        if (k + 1 < ke) v.y = __ldg(p + 1);
+        if (k + 2 < ke) v.z = __ldg(p + 2);
+      }
+    }
+  } else {
+    if (k < ke) {
+      const float* p = A + m + (int64_t)kk * lda;
+      if (m + 3 < g.M) {
+        v = __ldg(reinterpret_cast<const float4*>(p));
+      } else {
+        if (m < g.M) v.x = __ldg(p);
+        if (m + 1 < g.M) v.y = __ldg(p + 1);
+        if (m + 2 < g.M) v.z = __ldg(p + 2);
+      }
+    }
+  }
+  if (rnd) {
+    v.x = round_bf16(v.x);
+    v.y = round_bf16(v.y);
+    v.z = round_bf16(v.z);
+    v.w = round_bf16(v.w);
+  }
+  return v;
+}
+
+template <bool BKM>
+__device__ __forceinline__ float4 ld_b4(const GemmArgs& g, int k, int n, int ke, bool rnd) {
+  const float* B;
+  int64_t ldb;
+  int kk = k;
+  if (k < g.K0) {
+    B = (const float*)g.B0;
+    ldb = g.ldb0;
+  } else {
+    B = (const float*)g.B1;
+    ldb = g.ldb1;
+    kk = k - g.K0;
+  }
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (BKM) {
+    if (n < g.N) {
+      const float* p = B + (int64_t)n * ldb + kk;
+      if (k + 3 < ke) {
+        v = __ldg(reinterpret_cast<const float4*>(p));
+      } else {
+        if (k < ke) v.x = __ldg(p);
+        if (k + 1 < ke) v.y = __ldg(p + 1);
+        if (k + 2 < ke) v.z = __ldg(p + 2);
+      }
+    }
+  } else {
+    if (k < ke) {
+      const float* p = B + (int64_t)kk * ldb + n;
+      if (n + 3 < g.N) {
+        v = __ldg(reinterpret_cast<const float4*>(p));
+      } else {
+        if (n < g.N) v.x = __ldg(p);
+        if (n + 1 < g.N) v.y = __ldg(p + 1);
+        if (n + 2 < g.N) v.z = __ldg(p + 2);
+      }
+    }
+  }
+  if (rnd) {
+    v.x = round_bf16(v.x);
+    v.y = round_bf16(v.y);
+    v.z = round_bf16(v.z);
+    v.w = round_bf16(v.w);
+  }
+  return v;
+}
+
+template <bool AK, bool BKM>
+__global__ void __launch_bounds__(LNT) sgemm_large_kernel(const GemmArgs g) {
+  __shared__ __align__(16) float As[2][LBK][LBM];
+  __shared__ __align__(16) float Bs[2][LBK][LBN];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int m0 = blockIdx.y * LBM, n0 = blockIdx.x * LBN;
+  const int K = g.K0 + g.K1;
+  const int kb = blockIdx.z * g.k_chunk;
+  const int ke = min(K, kb + g.k_chunk);
+  const bool rnd = g.round_bf16;
+  // global-load coordinates of this thread's 16-byte piece of each tile
+  const int am = AK ? (tid >> 1) : ((tid & 31) << 2);
+  const int ak = AK ? ((tid & 1) << 2) : (tid >> 5);
+  const int bn = BKM ? (tid >> 1) : ((tid & 31) << 2);
+  const int bk = BKM ? ((tid & 1) << 2) : (tid >> 5);
+
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+  auto store_tile = [&](int buf, const float4& va, const float4& vb) {
+    if (AK) {
+      As[buf][ak + 0][am] = va.x;
+      As[buf][ak + 1][am] = va.y;
+      As[buf][ak + 2][am] = va.z;
+      As[buf][ak + 3][am] = va.w;
+    } else {
+      *reinterpret_cast<float4*>(&As[buf][ak][am]) = va;
+    }
+    if (BKM) {
+      Bs[buf][bk + 0][bn] = vb.x;
+      Bs[buf][bk + 1][bn] = vb.y;
+      Bs[buf][bk + 2][bn] = vb.z;
+      Bs[buf][bk + 3][bn] = vb.w;
+    } else {
+      *reinterpret_cast<float4*>(&Bs[buf][bk][bn]) = vb;
+    }
+  };
+
+  int buf = 0;
+  if (kb < ke) {
+    const float4 va = ld_a4<AK>(g, m0 + am, kb + ak, ke, rnd);
+    const float4 vb = ld_b4<BKM>(g, kb + bk, n0 + bn, ke, rnd);
+    store_tile(0, va, vb);
+  }
+  __syncthreads();
+  for (int kt = kb; kt < ke; kt += LBK) {
+    const bool more = kt + LBK < ke;
+    float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
+    if (more) {
+      na = ld_a4<AK>(g, m0 + am, kt + LBK + ak, ke, rnd);
+      nb = ld_b4<BKM>(g, kt + LBK + bk, n0 + bn, ke, rnd);
+    }
+#pragma unroll
+    for (int kk = 0; kk < LBK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) store_tile(buf ^ 1, na, nb);
+    __syncthreads();
+    buf ^= 1;
+  }
+
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+      if (m < g.M && n < g.N) {
+        if (g.splits == 1)
+          epilogue_store<float, float>(g, m, n, acc[i][j]);
+        else
+          ((float*)g.partial)[(int64_t)blockIdx.z * g.M * g.N + (int64_t)m * g.N + n] = acc[i][j];
+      }
+    }
+  }
+}
+
+bool large_ok(const GemmArgs& g) {
+  auto al = [](const void* p) { return p == nullptr || ((uintptr_t)p % 16) == 0; };
+  if (g.sym) return false;
+  if ((int64_t)g.M * g.N < 128 * 128 * 8) return false;  // small outputs: the 64 x 64 kernel
+  if (g.K0 % LBK != 0 && g.K1 > 0) return false;
+  if (!al(g.A0) || !al(g.A1) || !al(g.B0) || !al(g.B1)) return false;
+  if (g.lda0 % 4 || g.ldb0 % 4 || (g.K1 > 0 && (g.lda1 % 4 || g.ldb1 % 4))) return false;
+  return true;
+}
+
+int run_large_f32(const GemmArgs& g, cudaStream_t s) {
+  const int K = g.K0 + g.K1;
+  GemmArgs a = g;
+  if (a.splits < 1) a.splits = 1;
+  if (a.splits > 1 && K > 0) {
+    a.k_chunk = (int)round_up(ceil_div(K, a.splits), 16);
+    a.splits = (int)ceil_div(K, a.k_chunk);
+  } else {
+    a.splits = 1;
+    a.k_chunk = (int)round_up(std::max(K, 1), 16);
+  }
+  dim3 grid((unsigned)ceil_div(a.N, LBN), (unsigned)ceil_div(a.M, LBM), (unsigned)a.splits);
+  if (a.a_kmaj && a.b_kmaj)
+    sgemm_large_kernel<true, true><<<grid, LNT, 0, s>>>(a);
+  else if (a.a_kmaj && !a.b_kmaj)
+    sgemm_large_kernel<true, false><<<grid, LNT, 0, s>>>(a);
+  else if (!a.a_kmaj && a.b_kmaj)
+    sgemm_large_kernel<false, true><<<grid, LNT, 0, s>>>(a);
+  else
+    sgemm_large_kernel<false, false><<<grid, LNT, 0, s>>>(a);
+  note_launches(1);
+  if (a.splits > 1) {
+    int64_t total = (int64_t)a.M * a.N;
+    int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
+    splitk_reduce<float, float><<<blocks, 256, 0, s>>>(a);
+    note_launches(1);
+  }
+  return (int)cudaGetLastError();
 }
 
 template <typename TIn, typename Acc, typename TOut>
@@ -215,9 +529,38 @@ int gemm_pick_splits(int M, int N, int K, int /*sm_count*/) {
   return (int)s;
 }
 
+int gram_run_comp(const GemmArgs& g, cudaStream_t s) {
+  if (g.M <= 0) return (int)cudaSuccess;
+  GemmArgs a = g;
+  const int K = a.K0;
+  a.sym = true;
+  a.splits = std::max(a.splits, 1);
+  a.k_chunk = (int)round_up(std::max<int64_t>(ceil_div(std::max(K, 1), a.splits), 1), BKK);
+  a.splits = (int)std::max<int64_t>(1, ceil_div(std::max(K, 1), a.k_chunk));
+  dim3 grid((unsigned)ceil_div(a.N, BN), (unsigned)ceil_div(a.M, BM), (unsigned)a.splits);
+  gram_comp_kernel<<<grid, NT, 0, s>>>(a);
+  const int64_t total = (int64_t)a.M * a.N;
+  const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
+  splitk_reduce<double, double><<<blocks, 256, 0, s>>>(a);
+  note_launches(2);
+  return (int)cudaGetLastError();
+}
+
 int gemm_run(const GemmArgs& g, DType in_t, DType acc_t, DType out_t, cudaStream_t s) {
   if (in_t == DT_F64 && acc_t == DT_F64 && out_t == DT_F64) return run_typed<double, double, double>(g, s);
-  if (in_t == DT_F32 && acc_t == DT_F32 && out_t == DT_F32) return run_typed<float, float, float>(g, s);
+  if (in_t == DT_F32 && acc_t == DT_F32 && out_t == DT_F32) {
+    if (large_ok(g)) {
+      // enough CTAs for the GPU: split K when the output has few 128 x 128 tiles
+      GemmArgs a = g;
+      const int64_t tiles = ceil_div(g.M, LBM) * ceil_div(g.N, LBN);
+      const int64_t room = a.partial ? (int64_t)(a.partial_bytes / ((size_t)g.M * g.N * sizeof(float))) : 0;
+      if (a.splits <= 1 && tiles < 152 && room >= 2)
+        a.splits = (int)std::min<int64_t>(std::min<int64_t>(4, 304 / tiles), room);
+      if (a.splits > 1 && room < a.splits) a.splits = (int)std::max<int64_t>(1, room);
+      return run_large_f32(a, s);
+    }
+    return run_typed<float, float, float>(g, s);
+  }
   if (in_t == DT_F32 && acc_t == DT_F64 && out_t == DT_F64) return run_typed<float, double, double>(g, s);
   return (int)cudaErrorInvalidValue;
 }

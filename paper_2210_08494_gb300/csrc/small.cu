@@ -10,6 +10,7 @@
 //   * the damping coefficients of the inverse application (Algorithm 1) with
 //     optional spectrum continuation (Sec. 3.5.1).
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 
@@ -72,29 +73,38 @@ __global__ void __launch_bounds__(1024) chol_kernel(const double* __restrict__ G
                                                     const double* scale) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const double thr = thr_rel * (scale ? *scale : 1.0);
-  for (int e = tid; e < n * n; e += nt) {
-    const int i = e % n, l = e / n;
-    R[e] = (i <= l) ? Gm[e] : 0.0;
-  }
+  for (int l = 0; l < n; ++l)
+    for (int i = tid; i < n; i += nt) R[i + l * n] = (i <= l) ? Gm[i + l * n] : 0.0;
   __syncthreads();
+  __shared__ double s_piv[2];
+  __shared__ int s_keep;
   for (int j = 0; j < n; ++j) {
-    const double s = R[j + (int64_t)j * n];
-    const bool keep = s > thr;  // false for NaN as well
-    if (!isfinite(s) && tid == 0) report(BKFAC_ENONFINITE);
-    __syncthreads();  // everyone has read the pivot before it is overwritten
+    if (tid == 0) {
+      // one thread takes the pivot's square root and reciprocal (long FP64 sequences)
+      const double s = R[j + (int64_t)j * n];
+      s_keep = s > thr;  // false for NaN as well
+      if (!isfinite(s)) report(BKFAC_ENONFINITE);
+      if (s_keep) {
+        s_piv[0] = sqrt(s);
+        s_piv[1] = 1.0 / s_piv[0];
+      }
+    }
+    __syncthreads();
+    const bool keep = s_keep;
     if (keep) {
-      const double rjj = sqrt(s);
-      const double inv = 1.0 / rjj;
+      const double rjj = s_piv[0];
+      const double inv = s_piv[1];
       for (int l = j + tid; l < n; l += nt) R[j + (int64_t)l * n] = (l == j) ? rjj : R[j + (int64_t)l * n] * inv;
     } else {
       for (int l = j + tid; l < n; l += nt) R[j + (int64_t)l * n] = 0.0;
     }
     __syncthreads();
     if (keep) {
-      const int m = n - j - 1;
-      for (int e = tid; e < m * m; e += nt) {
-        const int i = j + 1 + e % m, l = j + 1 + e / m;
-        if (i <= l) R[i + (int64_t)l * n] -= R[j + (int64_t)i * n] * R[j + (int64_t)l * n];
+      // trailing update, a warp per column l, lanes over rows i in (j, l]
+      const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+      for (int l = j + 1 + wid; l < n; l += nw) {
+        const double rjl = R[j + (int64_t)l * n];
+        for (int i = j + 1 + lane; i <= l; i += 32) R[i + (int64_t)l * n] -= R[j + (int64_t)i * n] * rjl;
       }
     }
     __syncthreads();
@@ -102,28 +112,51 @@ __global__ void __launch_bounds__(1024) chol_kernel(const double* __restrict__ G
 }
 
 // ---------------------------------------------------------------- triangular inverse
-// one warp per column j of Rinv: back substitution R x = e_j, the dot products
-// split over the lanes.  Zero diagonal (dropped pivot) -> zero row/column.
-template <typename T>
+// One warp per column j of Rinv, solving R x = e_j by column sweeps:
+//   for l = j, j-1, ..., 0:  x_l = y_l / R_ll;  y_i -= R_il x_l  (i < l, lanes over i)
+// so each step is a broadcast and an axpy -- no warp reduction on the critical
+// path.  Zero diagonal (dropped pivot) -> zero row/column.  R's upper triangle
+// is staged in shared memory packed by columns (column l holds rows 0..l), in
+// the working type, when it fits; otherwise it is read from global memory.
+__host__ __device__ __forceinline__ int64_t packed_col(int l) { return (int64_t)l * (l + 1) / 2; }
+
+template <typename T, bool SMEM>
 __global__ void __launch_bounds__(1024) trinv_kernel(const double* __restrict__ R, int n, T* Rinv) {
-  const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * 32 + (threadIdx.x >> 5);
-  if (j >= n) return;
-  T* x = Rinv + (int64_t)j * n;
-  for (int i = lane; i < n; i += 32) x[i] = T(0);
-  __syncwarp();
-  const double rjj = R[j + (int64_t)j * n];
-  if (lane == 0) x[j] = rjj != 0.0 ? (T)(1.0 / rjj) : T(0);
-  __syncwarp();
-  for (int i = j - 1; i >= 0; --i) {
+  extern __shared__ __align__(16) unsigned char tr_smem[];
+  T* inv = (T*)tr_smem;                                  // reciprocal diagonal (0 for dropped pivots)
+  T* Rs = inv + n;                                       // packed upper triangle by columns (SMEM only)
+  T* ys = Rs + (SMEM ? packed_col(n) : 0);               // one working column per warp
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double rii = R[i + (int64_t)i * n];
-    T s = T(0);
-    for (int l = i + 1 + lane; l <= j; l += 32) s += (T)R[i + (int64_t)l * n] * x[l];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) x[i] = rii != 0.0 ? (T)(-(double)s / rii) : T(0);
+    inv[i] = rii != 0.0 ? (T)(1.0 / rii) : T(0);
+  }
+  if (SMEM) {
+    for (int l = wid; l < n; l += blockDim.x >> 5)
+      for (int i = lane; i <= l; i += 32) Rs[packed_col(l) + i] = (T)R[i + (int64_t)l * n];
+  }
+  __syncthreads();
+  const int j = blockIdx.x * 32 + wid;
+  if (j >= n) return;
+  T* y = ys + (int64_t)wid * n;
+  for (int i = lane; i < n; i += 32) y[i] = (i == j) ? T(1) : T(0);
+  __syncwarp();
+  for (int l = j; l >= 0; --l) {
+    const T xl = y[l] * inv[l];  // broadcast read
+    __syncwarp();
+    if (lane == 0) y[l] = xl;
+    if (xl != T(0)) {
+      if (SMEM) {
+        const T* col = Rs + packed_col(l);
+        for (int i = lane; i < l; i += 32) y[i] -= col[i] * xl;
+      } else {
+        for (int i = lane; i < l; i += 32) y[i] -= (T)R[i + (int64_t)l * n] * xl;
+      }
+    }
     __syncwarp();
   }
+  T* out = Rinv + (int64_t)j * n;
+  for (int i = lane; i < n; i += 32) out[i] = i <= j ? y[i] : T(0);
 }
 
 // ---------------------------------------------------------------- core factor L
@@ -222,9 +255,11 @@ __global__ void __launch_bounds__(256) assemble_reorth_kernel(const double* R, c
 // to ||W||_F^2) are returned as zero vectors with sigma = 0.
 template <typename J, typename TO>
 __global__ void __launch_bounds__(1024) sort_output_kernel(const SortArgs a) {
-  extern __shared__ double lam[];  // cols
+  // norms, ordering and scaling in the Jacobi type J (FP32 arithmetic for the FP32
+  // paths); only the eigenvalues handed back are widened to double
+  extern __shared__ __align__(16) unsigned char so_smem[];
+  J* lam = (J*)so_smem;  // cols
   int* rank = (int*)(lam + a.cols);
-  __shared__ double red[32];
   __shared__ double s_tiny;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const J* W = (const J*)a.W;
@@ -237,41 +272,45 @@ __global__ void __launch_bounds__(1024) sort_output_kernel(const SortArgs a) {
   }
   for (int i = wid; i < a.cols; i += nw) {
     const J* w = W + (int64_t)i * a.rows_pad;
-    double s = 0.0;
-    for (int r = lane; r < a.rows; r += 32) {
-      const double v = (double)w[r];
-      s += v * v;
+    J s0 = J(0), s1 = J(0);
+    int r = lane;
+    for (; r + 32 < a.rows; r += 64) {
+      const J v0 = w[r], v1 = w[r + 32];
+      s0 += v0 * v0;
+      s1 += v1 * v1;
     }
-    s = warp_sum(s);
-    if (lane == 0) lam[i] = s;
+    if (r < a.rows) s0 += w[r] * w[r];
+    J sum = s0 + s1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) lam[i] = sum;
   }
   __syncthreads();
-  const double tiny = s_tiny;
+  const J tiny = (J)s_tiny;
   for (int i = threadIdx.x; i < a.cols; i += blockDim.x) {
-    const double li = lam[i];
+    const J li = lam[i];
     int rk = 0;
     for (int j = 0; j < a.cols; ++j) {
-      const double lj = lam[j];
+      const J lj = lam[j];
       rk += (lj > li) || (lj == li && j < i);
     }
     rank[i] = rk;
     if (!isfinite(li)) report(BKFAC_ENONFINITE);
-    if (a.lam_sorted) a.lam_sorted[rk] = li;
-    if (rk < a.r_out && a.sig) a.sig[rk] = li > tiny ? li : 0.0;
+    if (a.lam_sorted) a.lam_sorted[rk] = (double)li;
+    if (rk < a.r_out && a.sig) a.sig[rk] = li > tiny ? (double)li : 0.0;
   }
   if (a.sig)
     for (int j = a.r_out + threadIdx.x; j < a.r_sig; j += blockDim.x) a.sig[j] = 0.0;
   __syncthreads();
-  (void)red;
   // write the selected columns, one warp per column
   for (int i = wid; i < a.cols; i += nw) {
     const int rk = rank[i];
     if (rk >= a.r_out) continue;
-    const double li = lam[i];
-    const double inv = li > tiny ? 1.0 / sqrt(li) : 0.0;
+    const J li = lam[i];
+    const J sc = li > tiny ? J(1) / sqrt(li) : J(0);
     const J* w = W + (int64_t)i * a.rows_pad;
     TO* v = (TO*)a.V + (int64_t)rk * a.ldv;
-    for (int r = lane; r < a.rows; r += 32) v[r] = (TO)((double)w[r] * inv);
+    for (int r = lane; r < a.rows; r += 32) v[r] = (TO)(w[r] * sc);
   }
 }
 
@@ -279,11 +318,10 @@ __global__ void __launch_bounds__(1024) sort_output_kernel(const SortArgs a) {
 template <typename T>
 __global__ void __launch_bounds__(256) finalize_kernel(T* U, int64_t ldu, const T* Un, int64_t ldn, int d, int r_new,
                                                        int r) {
-  const int64_t total = (int64_t)d * r;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % d), j = (int)(e / d);
-    U[i + (int64_t)j * ldu] = j < r_new ? Un[i + (int64_t)j * ldn] : T(0);
-  }
+  // a block row of threads per column: grid.y over columns, grid.x over rows
+  for (int j = blockIdx.y; j < r; j += gridDim.y)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x)
+      U[i + (int64_t)j * ldu] = j < r_new ? Un[i + (int64_t)j * ldn] : T(0);
 }
 
 // ---------------------------------------------------------------- apply coefficients
@@ -337,13 +375,29 @@ int launch_chol(const double* Gm, int n, double* R, double thr_rel, const double
   return (int)cudaGetLastError();
 }
 
+template <typename T>
+void trinv_launch(const double* R, int n, T* Rinv, cudaStream_t s) {
+  static std::atomic<int> configured{0};  // attribute set once (the call can stall the host)
+  if (!configured.load()) {
+    cudaFuncSetAttribute(trinv_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(trinv_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    configured.store(1);
+  }
+  const int blocks = (int)ceil_div(n, 32);
+  const size_t xs = (size_t)32 * n * sizeof(T) + (size_t)n * sizeof(T);
+  const size_t rs = (size_t)(packed_col(n)) * sizeof(T);
+  if (rs + xs <= 220 * 1024)
+    trinv_kernel<T, true><<<blocks, 1024, rs + xs, s>>>(R, n, Rinv);
+  else
+    trinv_kernel<T, false><<<blocks, 1024, xs, s>>>(R, n, Rinv);
+}
+
 int launch_trinv(const double* R, int n, void* Rinv, DType t, cudaStream_t s) {
   if (n <= 0) return 0;
-  const int blocks = (int)ceil_div(n, 32);
   if (t == DT_F64)
-    trinv_kernel<double><<<blocks, 1024, 0, s>>>(R, n, (double*)Rinv);
+    trinv_launch<double>(R, n, (double*)Rinv, s);
   else
-    trinv_kernel<float><<<blocks, 1024, 0, s>>>(R, n, (float*)Rinv);
+    trinv_launch<float>(R, n, (float*)Rinv, s);
   note_launches(1);
   return (int)cudaGetLastError();
 }
@@ -384,34 +438,39 @@ int launch_assemble_reorth(const double* R, const double* sigma, int k, int rows
   return (int)cudaGetLastError();
 }
 
-int launch_sort_output(const SortArgs& a, DType j_t, DType out_t, cudaStream_t s) {
-  const size_t smem = (size_t)a.cols * (sizeof(double) + sizeof(int));
-  if (smem > 200 * 1024) return (int)cudaErrorInvalidValue;
-  if (j_t == DT_F64 && out_t == DT_F64) {
-    cudaFuncSetAttribute(sort_output_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    sort_output_kernel<double, double><<<1, 1024, smem, s>>>(a);
-  } else if (j_t == DT_F32 && out_t == DT_F32) {
-    cudaFuncSetAttribute(sort_output_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    sort_output_kernel<float, float><<<1, 1024, smem, s>>>(a);
-  } else if (j_t == DT_F64 && out_t == DT_F32) {
-    cudaFuncSetAttribute(sort_output_kernel<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    sort_output_kernel<double, float><<<1, 1024, smem, s>>>(a);
-  } else {
-    cudaFuncSetAttribute(sort_output_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    sort_output_kernel<float, double><<<1, 1024, smem, s>>>(a);
+template <typename J, typename TO>
+void sort_launch(const SortArgs& a, size_t smem, cudaStream_t s) {
+  static std::atomic<int> configured{0};  // attribute set once (the call can stall the host)
+  if (!configured.load()) {
+    cudaFuncSetAttribute(sort_output_kernel<J, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    configured.store(1);
   }
+  sort_output_kernel<J, TO><<<1, 1024, smem, s>>>(a);
+}
+
+int launch_sort_output(const SortArgs& a, DType j_t, DType out_t, cudaStream_t s) {
+  const size_t smem = (size_t)a.cols * (sizeof(double) + sizeof(int));  // bound for either J
+  if (smem > 200 * 1024) return (int)cudaErrorInvalidValue;
+  if (j_t == DT_F64 && out_t == DT_F64)
+    sort_launch<double, double>(a, smem, s);
+  else if (j_t == DT_F32 && out_t == DT_F32)
+    sort_launch<float, float>(a, smem, s);
+  else if (j_t == DT_F64 && out_t == DT_F32)
+    sort_launch<double, float>(a, smem, s);
+  else
+    sort_launch<float, double>(a, smem, s);
   note_launches(1);
   return (int)cudaGetLastError();
 }
 
 int launch_finalize(void* U, int64_t ldu, const void* Unew, int64_t ldn, int d, int r_new, int r, DType t,
                     cudaStream_t s) {
-  const int64_t total = (int64_t)d * r;
-  const int blocks = (int)std::min<int64_t>(std::max<int64_t>(1, ceil_div(total, 256)), 2048);
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(d, 256), 16)),
+                  (unsigned)std::max(1, std::min(r, 1024)));
   if (t == DT_F64)
-    finalize_kernel<double><<<blocks, 256, 0, s>>>((double*)U, ldu, (const double*)Unew, ldn, d, r_new, r);
+    finalize_kernel<double><<<grid, 256, 0, s>>>((double*)U, ldu, (const double*)Unew, ldn, d, r_new, r);
   else
-    finalize_kernel<float><<<blocks, 256, 0, s>>>((float*)U, ldu, (const float*)Unew, ldn, d, r_new, r);
+    finalize_kernel<float><<<grid, 256, 0, s>>>((float*)U, ldu, (const float*)Unew, ldn, d, r_new, r);
   note_launches(1);
   return (int)cudaGetLastError();
 }

@@ -67,6 +67,8 @@ TraceScope::~TraceScope() {
 
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+int64_t launch_count() { return g_launches.load(); }
+
 }  // namespace bkfac
 
 using namespace bkfac;
