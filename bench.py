@@ -407,7 +407,7 @@ def run_mlp(args, world, rank, local):
 def run_gpu(args, world, rank, local):
     import torch
 
-    from paper_2210_08494_gb300 import bkfac, synth
+    from paper_2210_08494_gb300 import bkfac, shard, synth
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -478,11 +478,7 @@ def run_gpu(args, world, rank, local):
     st = bkfac.bkfac_status()
     if st != bkfac.OK:
         raise RuntimeError(f"device status after timed region: {bkfac.strerror(st)}")
-    ms_total = float(sum(a.elapsed_time(b) for a, b in evs))
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = shard.max_over_ranks(float(sum(a.elapsed_time(b) for a, b in evs)), device=dev)
     ms_step = ms_total / args.steps
     steps_per_s = 1000.0 / ms_step
     value = 2.0 * steps_per_s * world

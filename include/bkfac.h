@@ -288,6 +288,11 @@ int bkfac_batch_step_graph(bkfac_batch* b, const void* const* X_A, const int64_t
                            void* const* S, const int64_t* lds, const double* lamA, const double* lamG,
                            uint32_t flags, int capture, bkfac_stream_t stream);
 
+/* Re-orthonormalises every factor of the batch (bkfac_reorth on each, forked over
+ * the worker streams): the periodic accuracy recovery of the mixed-precision path,
+ * e.g. every 10 steps. */
+int bkfac_batch_reorth(bkfac_batch* b, bkfac_stream_t stream);
+
 void bkfac_batch_destroy(bkfac_batch* b);
 
 #ifdef __cplusplus

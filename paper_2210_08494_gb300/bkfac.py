@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True):
                                         ctypes.POINTER(P), ctypes.POINTER(I64), ctypes.POINTER(D),
                                         ctypes.POINTER(D), U32, I, P], I),
             "bkfac_batch_destroy": ([P], None),
+            "bkfac_batch_reorth": ([P, P], I),
             "bkfac_trace_enable": ([I], I),
             "bkfac_tune": ([FP, I, ctypes.c_char_p], I),
             "bkfac_trace_read": ([ctypes.POINTER(D), ctypes.POINTER(I64), I, ctypes.POINTER(I64)], I),
@@ -114,7 +115,7 @@ def exported_symbols():
               "bkfac_apply_workspace_size", "bkfac_init", "bkfac_update", "bkfac_reorth", "bkfac_apply",
               "bkfac_debug_offsets", "bkfac_batch_create", "bkfac_batch_get_factor", "bkfac_batch_update",
               "bkfac_batch_apply", "bkfac_batch_step_graph", "bkfac_batch_destroy", "bkfac_trace_enable",
-              "bkfac_trace_read", "bkfac_trace_phase_name", "bkfac_apply_noalloc", "bkfac_tune"):
+              "bkfac_trace_read", "bkfac_trace_phase_name", "bkfac_apply_noalloc", "bkfac_tune", "bkfac_batch_reorth"):
         if hasattr(lib, n):
             names.append(n)
     return names
@@ -373,6 +374,9 @@ class Batch:
         else:
             _check(lib.bkfac_batch_step_graph(self.h, None, None, None, None, 0.0, None, None, None, None, None,
                                               None, int(flags), 0, _stream(stream)), "bkfac_batch_step_graph")
+
+    def reorth(self, stream=None):
+        _check(load().bkfac_batch_reorth(self.h, _stream(stream)), "bkfac_batch_reorth")
 
     def close(self):
         if getattr(self, "h", None):

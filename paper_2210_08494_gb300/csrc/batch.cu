@@ -21,6 +21,7 @@ struct bkfac_batch {
   void* ws = nullptr;
   std::vector<size_t> ws_off, ws_len;        // per factor (update)
   std::vector<size_t> aws_off, aws_len;      // per layer (apply)
+  std::vector<size_t> rws_off, rws_len;      // per factor (reorth)
   std::vector<cudaStream_t> streams;         // per factor
   std::vector<cudaEvent_t> done;             // per factor
   cudaEvent_t fork = nullptr;
@@ -134,6 +135,15 @@ bkfac_batch* bkfac_batch_create(const bkfac_layer_desc* layers, int nlayers, int
       b->ws_len.push_back(sz);
     }
   }
+  for (int i = 0; i < 2 * nlayers; ++i) {
+    const size_t sz = bkfac_workspace_size(&b->f[i], n, BKFAC_OP_REORTH);
+    if (sz == 0) {
+      destroy(b);
+      return nullptr;
+    }
+    b->rws_off.push_back(carve(sz));
+    b->rws_len.push_back(sz);
+  }
   for (int l = 0; l < nlayers; ++l) {
     const size_t sz = bkfac_apply_workspace_size(&b->f[2 * l], &b->f[2 * l + 1]);
     if (sz == 0) {
@@ -233,6 +243,21 @@ int bkfac_batch_step_graph(bkfac_batch* b, const void* const* X_A, const int64_t
   note_launches((int)b->graph_kernels);
   for (auto& f : b->f) f.step += 1;
   return BKFAC_OK;
+}
+
+int bkfac_batch_reorth(bkfac_batch* b, bkfac_stream_t stream) {
+  if (!b) return BKFAC_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int nf = 2 * b->nl;
+  int rc = fork_from(b, s, nf);
+  if (rc) return rc;
+  int first_err = BKFAC_OK;
+  for (int i = 0; i < nf; ++i) {
+    rc = bkfac_reorth(&b->f[i], (char*)b->ws + b->rws_off[i], b->rws_len[i], (bkfac_stream_t)b->streams[i]);
+    if (rc && !first_err) first_err = rc;
+  }
+  rc = join_into(b, s, nf);
+  return first_err ? first_err : rc;
 }
 
 void bkfac_batch_destroy(bkfac_batch* b) { destroy(b); }
