@@ -168,6 +168,10 @@ int bkfac_reorth(bkfac_factor* f, void* ws, size_t ws_bytes, bkfac_stream_t stre
 /* Damped inverse application to one layer's gradient (Algorithm 1):
  *   S = (U_G C_G U_G^T + I/lam_G) G (U_A C_A U_A^T + I/lam_A),
  *   C = diag(1/(sigma + lam) - 1/lam) over the r_cur stored modes.
+ * A factor whose basis is complete (r_cur == d, e.g. a dense-path factor)
+ * has no complement: its side is applied as U diag(1/(sigma + lam)) U^T, the
+ * same operator in exact arithmetic, without the 1/lam identity term (whose
+ * cancellation against U C U^T a rounded basis would not reproduce).
  * Computed in two passes over G:
  *   pass 1  T1 = G U_A (d_out x r_A), T2 = U_G^T G (r_G x d_in);
  *   small   T3 = U_G^T T1, W1 = T1 C_A / lam_G + U_G (C_G T3 C_A), W2 = C_G T2 / lam_A;

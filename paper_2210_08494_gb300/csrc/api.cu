@@ -695,6 +695,8 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
   ca.lamA = lamA;
   ca.lamG = lamG;
   ca.continuation = (flags & BKFAC_SPECTRUM_CONTINUATION) ? 1 : 0;
+  ca.completeA = kA == dA ? 1 : 0;
+  ca.completeG = kG == dG ? 1 : 0;
   ca.cA = cA;
   ca.cG = cG;
   ca.cA_over = cAo;

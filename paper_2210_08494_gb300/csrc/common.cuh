@@ -204,6 +204,7 @@ struct ApplyCoefArgs {
   int kG;
   double lamA, lamG;
   int continuation;
+  int completeA, completeG;  // r_cur == d: the basis spans R^d and the 1/lambda complement is empty
   double* cA;        // kA: C_A
   double* cG;        // kG: C_G
   double* cA_over;   // kA: C_A / lamG'

@@ -340,17 +340,23 @@ __global__ void __launch_bounds__(256) apply_coefs_kernel(const ApplyCoefArgs a)
   __syncthreads();
   const double shA = smin[0], shG = smin[1];
   const double lA = a.lamA + shA, lG = a.lamG + shG;
+  // (U Sigma U^T + lambda I)^-1 = beta I + U C U^T with beta = 1/lambda' for the
+  // complement of span(U) and C = (Sigma + lambda)^-1 - beta.  A complete basis
+  // (r_cur = d) leaves no complement: beta = 0 and C = (Sigma + lambda)^-1, the same
+  // operator without the cancellation of beta I against U (-beta) U^T, which
+  // rounded (BF16) bases do not reproduce.
+  const double bA = a.completeA ? 0.0 : 1.0 / lA, bG = a.completeG ? 0.0 : 1.0 / lG;
   for (int i = threadIdx.x; i < a.kA; i += blockDim.x) {
-    const double c = 1.0 / ((a.sigA[i] - shA) + lA) - 1.0 / lA;
+    const double c = 1.0 / ((a.sigA[i] - shA) + lA) - bA;
     a.cA[i] = c;
-    a.cA_over[i] = c / lG;
+    a.cA_over[i] = c * bG;
   }
   for (int i = threadIdx.x; i < a.kG; i += blockDim.x) {
-    const double c = 1.0 / ((a.sigG[i] - shG) + lG) - 1.0 / lG;
+    const double c = 1.0 / ((a.sigG[i] - shG) + lG) - bG;
     a.cG[i] = c;
-    a.cG_over[i] = c / lA;
+    a.cG_over[i] = c * bA;
   }
-  if (threadIdx.x == 0) *a.alpha = 1.0 / (lA * lG);
+  if (threadIdx.x == 0) *a.alpha = bA * bG;
 }
 
 }  // namespace
