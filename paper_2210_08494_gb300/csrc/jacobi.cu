@@ -66,108 +66,57 @@ __device__ __forceinline__ J warp_sum_j(J v) {
 template <typename J>
 struct BigZeta;
 template <>
-struct BigZeta<float> {
-  static constexpr float v = 1e18f;
-};
-template <>
 struct BigZeta<double> {
   static constexpr double v = 1e150;
 };
 
-// column <-> registers: lane owns the 16-byte vectors lane + 32 k, k < NV
+// A lane's slice of one column: the 16-byte vectors lane + 32 k, k < NV.  FP32
+// keeps the slice as packed pairs of rows in 64-bit registers, so that every
+// product and rotation runs on Blackwell's two-wide FP32 FMA (fma.rn.f32x2)
+// without repacking; FP64 keeps plain doubles.
 template <typename J, int NV>
-__device__ __forceinline__ void load_col(const J* col, J (&x)[NV * Vec<J>::W], int lane) {
-  using V = typename Vec<J>::T;
-  const V* c = reinterpret_cast<const V*>(col);
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    const V v = c[lane + 32 * k];
-    const J* pv = reinterpret_cast<const J*>(&v);
-#pragma unroll
-    for (int w = 0; w < Vec<J>::W; ++w) x[k * Vec<J>::W + w] = pv[w];
-  }
-}
+struct Col;
 
-template <typename J, int NV>
-__device__ __forceinline__ void store_col(J* col, const J (&x)[NV * Vec<J>::W], int lane) {
-  using V = typename Vec<J>::T;
-  V* c = reinterpret_cast<V*>(col);
+template <int NV>
+struct Col<float, NV> {
+  static constexpr int P = 2 * NV;  // packed row pairs per lane
+  uint64_t v[P];
+  __device__ __forceinline__ void load(const float* col, int lane) {
+    const ulonglong2* c = reinterpret_cast<const ulonglong2*>(col);
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    V v;
-    J* pv = reinterpret_cast<J*>(&v);
-#pragma unroll
-    for (int w = 0; w < Vec<J>::W; ++w) pv[w] = x[k * Vec<J>::W + w];
-    c[lane + 32 * k] = v;
+    for (int k = 0; k < NV; ++k) {
+      const ulonglong2 q = c[lane + 32 * k];
+      v[2 * k] = q.x;
+      v[2 * k + 1] = q.y;
+    }
   }
-}
+  __device__ __forceinline__ void store(float* col, int lane) const {
+    ulonglong2* c = reinterpret_cast<ulonglong2*>(col);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) c[lane + 32 * k] = make_ulonglong2(v[2 * k], v[2 * k + 1]);
+  }
+};
 
-// Rotation parameters.  FP32 uses the hardware reciprocal / square-root
-// approximations: the angle need not be exact, and the update below applies
-// c and s in a form that stays orthogonal when c^2 + s^2 differs from 1 in the
-// last bits (the energy error is second order in s).  FP64 keeps IEEE division.
-__device__ __forceinline__ void rotation_params(float a, float b, float g, float& t, float& c, float& s) {
-  // hardware approximations only (reciprocal square root, fast division): the
-  // rotation need not be exact, only applied consistently (see rotate_regs_f2)
-  const float zeta = __fdividef(b - a, 2.0f * g);
-  const float az = fabsf(zeta);
-  if (az > BigZeta<float>::v) {
-    t = __fdividef(0.5f, zeta);
-  } else {
-    const float h = fmaf(az, az, 1.0f);
-    t = copysignf(__fdividef(1.0f, az + h * rsqrtf(h)), zeta);
-  }
-  c = rsqrtf(fmaf(t, t, 1.0f));
-  s = c * t;
-}
-__device__ __forceinline__ void rotation_params(double a, double b, double g, double& t, double& c, double& s) {
-  const double zeta = (b - a) / (2.0 * g);
-  const double az = fabs(zeta);
-  if (az > BigZeta<double>::v)
-    t = 0.5 / zeta;
-  else
-    t = copysign(1.0 / (az + sqrt(1.0 + az * az)), zeta);
-  c = 1.0 / sqrt(1.0 + t * t);
-  s = c * t;
-}
-
-// Orthogonalise the column pair (x, y) held in registers by the warp, given
-// their squared norms a = ||x||^2, b = ||y||^2 (tracked by the caller).  Only
-// the cross product g = x.y is reduced over the warp.  On a rotation the norms
-// are updated exactly as a' = a - t g, b' = b + t g.  Returns 1 if rotated.
-template <typename J, int E>
-__device__ __forceinline__ int rotate_regs_generic(J (&x)[E], J (&y)[E], J& a, J& b, J tol2, J tiny) {
-  J g0 = J(0), g1 = J(0);
+template <int NV>
+struct Col<double, NV> {
+  static constexpr int P = 2 * NV;  // doubles per lane
+  double v[P];
+  __device__ __forceinline__ void load(const double* col, int lane) {
+    const double2* c = reinterpret_cast<const double2*>(col);
 #pragma unroll
-  for (int e = 0; e < E; e += 2) {
-    g0 += x[e] * y[e];
-    if (e + 1 < E) g1 += x[e + 1] * y[e + 1];
+    for (int k = 0; k < NV; ++k) {
+      const double2 q = c[lane + 32 * k];
+      v[2 * k] = q.x;
+      v[2 * k + 1] = q.y;
+    }
   }
-  const J g = warp_sum_j(g0 + g1);
-  if (!(a > tiny && b > tiny && g * g > tol2 * a * b)) return 0;
-  // Rutishauser: zeta = (b - a) / (2 g), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))
-  J t, c, s;
-  rotation_params(a, b, g, t, c, s);
-  // Rutishauser's form with tau = tan(theta/2) = s / (1 + c): x' = x - s (y + tau x),
-  // y' = y + s (x - tau y).  It equals (c x - s y, s x + c y) but applies the O(t^2)
-  // shrink of x and y as an explicit correction, so for small angles (where 1 + t^2
-  // rounds to 1 and c = 1 exactly) the rotation stays orthogonal to working precision
-  // instead of growing both columns by (1 + t^2) -- a bias that otherwise
-  // accumulates over the thousands of rotations a column takes part in.
-  const J tau = s / (J(1) + c);  // c >= 1/sqrt(2): well conditioned
+  __device__ __forceinline__ void store(double* col, int lane) const {
+    double2* c = reinterpret_cast<double2*>(col);
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const J xv = x[e], yv = y[e];
-    x[e] = xv - s * (yv + tau * xv);
-    y[e] = yv + s * (xv - tau * yv);
+    for (int k = 0; k < NV; ++k) c[lane + 32 * k] = make_double2(v[2 * k], v[2 * k + 1]);
   }
-  a -= t * g;
-  b += t * g;
-  return 1;
-}
+};
 
-// FP32 specialisation with Blackwell's packed two-wide FP32 FMA (fma.rn.f32x2):
-// the dot product and the rotation process two rows per instruction.
 __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
   uint64_t d;
   asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
@@ -182,115 +131,274 @@ __device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
   return d;
 }
 
-template <int E>
-__device__ __forceinline__ int rotate_regs_f2(float (&x)[E], float (&y)[E], float& a, float& b, float tol2,
-                                              float tiny) {
-  static_assert(E % 4 == 0, "two packed chains of two rows");
-  uint64_t g0 = 0, g1 = 0;  // bit pattern of (0.f, 0.f)
+// this lane's part of x . y (two independent accumulation chains)
+template <int NV>
+__device__ __forceinline__ float dot_lane(const Col<float, NV>& x, const Col<float, NV>& y) {
+  constexpr int P = Col<float, NV>::P;
+  uint64_t g0 = 0, g1 = 0;  // bit patterns of (0.f, 0.f)
 #pragma unroll
-  for (int e = 0; e < E; e += 4) {
-    g0 = ffma2(pack2(x[e], x[e + 1]), pack2(y[e], y[e + 1]), g0);
-    g1 = ffma2(pack2(x[e + 2], x[e + 3]), pack2(y[e + 2], y[e + 3]), g1);
+  for (int e = 0; e < P; e += 2) {
+    g0 = ffma2(x.v[e], y.v[e], g0);
+    g1 = ffma2(x.v[e + 1], y.v[e + 1], g1);
   }
   float p0, p1, p2, p3;
   unpack2(g0, p0, p1);
   unpack2(g1, p2, p3);
-  const float g = warp_sum_j((p0 + p1) + (p2 + p3));
-  if (!(a > tiny && b > tiny && g * g > tol2 * a * b)) return 0;
-  float t, c, s;
-  rotation_params(a, b, g, t, c, s);
-  const float tau = __fdividef(s, 1.0f + c);
-  // tau form (see the generic version): x' = x - s (y + tau x), y' = y + s (x - tau y)
+  return (p0 + p1) + (p2 + p3);
+}
+template <int NV>
+__device__ __forceinline__ double dot_lane(const Col<double, NV>& x, const Col<double, NV>& y) {
+  constexpr int P = Col<double, NV>::P;
+  double g0 = 0.0, g1 = 0.0;
+#pragma unroll
+  for (int e = 0; e < P; e += 2) {
+    g0 = fma(x.v[e], y.v[e], g0);
+    g1 = fma(x.v[e + 1], y.v[e + 1], g1);
+  }
+  return g0 + g1;
+}
+
+// Rutishauser's form with tau = tan(theta/2) = s / (1 + c):
+//   x' = x - s (y + tau x),  y' = y + s (x - tau y).
+// It equals (c x - s y, s x + c y) but applies the O(theta^2) shrink of x and y
+// as an explicit correction, so small rotations (where c rounds to 1) stay
+// orthogonal to working precision instead of growing both columns by
+// (1 + t^2) -- a bias that would otherwise accumulate over the thousands of
+// rotations a column takes part in.
+template <int NV>
+__device__ __forceinline__ void rotate_lane(Col<float, NV>& x, Col<float, NV>& y, float s, float tau) {
   const uint64_t tau2 = pack2(tau, tau), ntau2 = pack2(-tau, -tau);
   const uint64_t s2 = pack2(s, s), ns2 = pack2(-s, -s);
 #pragma unroll
-  for (int e = 0; e < E; e += 2) {
-    const uint64_t xv = pack2(x[e], x[e + 1]), yv = pack2(y[e], y[e + 1]);
+  for (int e = 0; e < Col<float, NV>::P; ++e) {
+    const uint64_t xv = x.v[e], yv = y.v[e];
     const uint64_t u = ffma2(tau2, xv, yv);   // y + tau x
-    const uint64_t v = ffma2(ntau2, yv, xv);  // x - tau y
-    const uint64_t xn = ffma2(ns2, u, xv);
-    const uint64_t yn = ffma2(s2, v, yv);
-    unpack2(xn, x[e], x[e + 1]);
-    unpack2(yn, y[e], y[e + 1]);
+    const uint64_t w = ffma2(ntau2, yv, xv);  // x - tau y
+    x.v[e] = ffma2(ns2, u, xv);
+    y.v[e] = ffma2(s2, w, yv);
   }
-  a -= t * g;
-  b += t * g;
-  return 1;
 }
-
-// FP32 takes the packed path, FP64 the generic one
-template <typename J, int E>
-struct RotSel {
-  static __device__ __forceinline__ int run(J (&x)[E], J (&y)[E], J& a, J& b, J tol2, J tiny) {
-    return rotate_regs_generic<J, E>(x, y, a, b, tol2, tiny);
-  }
-};
-template <int E>
-struct RotSel<float, E> {
-  static __device__ __forceinline__ int run(float (&x)[E], float (&y)[E], float& a, float& b, float tol2,
-                                            float tiny) {
-    return rotate_regs_f2<E>(x, y, a, b, tol2, tiny);
-  }
-};
-template <typename J, int E>
-__device__ __forceinline__ int rotate_regs(J (&x)[E], J (&y)[E], J& a, J& b, J tol2, J tiny) {
-  return RotSel<J, E>::run(x, y, a, b, tol2, tiny);
-}
-
-template <typename J, int E>
-__device__ __forceinline__ J col_norm2(const J (&x)[E]) {
-  J a0 = J(0), a1 = J(0);
+template <int NV>
+__device__ __forceinline__ void rotate_lane(Col<double, NV>& x, Col<double, NV>& y, double s, double tau) {
 #pragma unroll
-  for (int e = 0; e < E; e += 2) {
-    a0 += x[e] * x[e];
-    if (e + 1 < E) a1 += x[e + 1] * x[e + 1];
+  for (int e = 0; e < Col<double, NV>::P; ++e) {
+    const double xv = x.v[e], yv = y.v[e];
+    x.v[e] = xv - s * (yv + tau * xv);
+    y.v[e] = yv + s * (xv - tau * yv);
   }
-  return warp_sum_j(a0 + a1);
+}
+
+// Rotation that zeroes the cross product g = x.y of two columns with squared
+// norms a, b: tan(2 theta) = 2 g / (a - b) with |theta| <= pi/4.  Outputs
+// s = sin(theta), tau = tan(theta / 2) and t g (t = tan(theta)), the amount by
+// which the squared norms move: a' = a - t g, b' = b + t g.
+//
+// FP32: a scale-free closed form on the hardware approximations.  With
+// d = (b - a)/(a + b) and h = 2 g/(a + b) (both in [-1, 1]), R = sqrt(d^2 + h^2)
+// and u = |d| + R:  cos = u / sqrt(2 R u),  sin = sign(d) h / sqrt(2 R u),
+// tan = sign(d) h / u -- three dependent approximations (rsqrt, rsqrt,
+// reciprocal) where the cotangent form needs five.  The angle need not be
+// exact; the tau form above keeps the applied rotation orthogonal.
+__device__ __forceinline__ void rotation_params(float a, float b, float g, float& s, float& tau, float& tg) {
+  const float rab = __fdividef(1.0f, a + b);
+  const float d = (b - a) * rab, h = 2.0f * g * rab;
+  const float q = fmaf(d, d, h * h);
+  const float R = q * rsqrtf(q);
+  const float u = fabsf(d) + R;
+  const float rp = rsqrtf(2.0f * R * u);
+  const float c = u * rp;
+  const float sh = d < 0.0f ? -h : h;  // sign(d) h
+  s = sh * rp;
+  tau = __fdividef(s, 1.0f + c);
+  tg = __fdividef(sh, u) * g;
+}
+// FP64: Rutishauser's cotangent form with IEEE division and square root.
+__device__ __forceinline__ void rotation_params(double a, double b, double g, double& s, double& tau, double& tg) {
+  const double zeta = (b - a) / (2.0 * g);
+  const double az = fabs(zeta);
+  double t;
+  if (az > BigZeta<double>::v)
+    t = 0.5 / zeta;
+  else
+    t = copysign(1.0 / (az + sqrt(1.0 + az * az)), zeta);
+  const double c = 1.0 / sqrt(1.0 + t * t);
+  s = c * t;
+  tau = s / (1.0 + c);
+  tg = t * g;
+}
+
+// "Transposed" warp reduction of K (1, 2 or 4) values: each of the first log2 K
+// butterfly levels exchanges half of the values still held, so that afterwards
+// every lane holds one running sum; the remaining levels are plain butterflies.
+// Lane l ends with the full sum of v[l / (32 / K)] (K - 1 + 5 - log2 K shuffles
+// instead of 5 K).
+template <typename J, int K>
+__device__ __forceinline__ J warp_sum_spread(const J (&v)[K], int lane) {
+  constexpr unsigned F = 0xffffffffu;
+  J t;
+  if constexpr (K == 4) {
+    const bool h = (lane & 16) != 0;
+    const J r0 = (h ? v[2] : v[0]) + __shfl_xor_sync(F, h ? v[0] : v[2], 16);
+    const J r1 = (h ? v[3] : v[1]) + __shfl_xor_sync(F, h ? v[1] : v[3], 16);
+    const bool q = (lane & 8) != 0;
+    t = (q ? r1 : r0) + __shfl_xor_sync(F, q ? r0 : r1, 8);
+    t += __shfl_xor_sync(F, t, 4);
+  } else if constexpr (K == 2) {
+    const bool h = (lane & 16) != 0;
+    t = (h ? v[1] : v[0]) + __shfl_xor_sync(F, h ? v[0] : v[1], 16);
+    t += __shfl_xor_sync(F, t, 8);
+    t += __shfl_xor_sync(F, t, 4);
+  } else {
+    t = v[0];
+    t += __shfl_xor_sync(F, t, 16);
+    t += __shfl_xor_sync(F, t, 8);
+    t += __shfl_xor_sync(F, t, 4);
+  }
+  t += __shfl_xor_sync(F, t, 2);
+  t += __shfl_xor_sync(F, t, 1);
+  return t;
+}
+
+// K independent column pairs (x[i], y[(i + SH) mod K]) held in registers by the
+// warp.  The K dot products are reduced with one spread reduction, after which
+// the lanes of group i (lanes [i 32/K, (i + 1) 32/K)) hold pair i's cross
+// product and compute that pair's rotation -- each group one pair, so the
+// angle arithmetic is issued once for all K pairs; the angles are then
+// broadcast and each pair whose cosine exceeds the tolerance is rotated.  a /
+// bn are the tracked squared norms of x / y, xs / ys the stamps (sweep of the
+// last rotation).  act bit i enables pair i.  Returns the rotated pairs as a
+// bit mask.
+template <typename J, int NV, int K, int SH>
+__device__ __forceinline__ unsigned step_pairs(Col<J, NV> (&x)[K], Col<J, NV> (&y)[K], J (&a)[K], J (&bn)[K],
+                                               int (&xs)[K], int (&ys)[K], unsigned act, int sweep, J tol2,
+                                               J tiny, int lane) {
+  if (act == 0) return 0;
+  constexpr int GL = 32 / K;  // lanes per pair group
+  J pd[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) pd[i] = dot_lane(x[i], y[(i + SH) % K]);
+  const J g = warp_sum_spread<J, K>(pd, lane);
+  const int me = lane / GL;
+  J am = a[0], bm = bn[SH % K];
+#pragma unroll
+  for (int i = 1; i < K; ++i)
+    if (me == i) {
+      am = a[i];
+      bm = bn[(i + SH) % K];
+    }
+  const bool on = ((act >> me) & 1u) && am > tiny && bm > tiny && g * g > tol2 * am * bm;
+  const unsigned bal = __ballot_sync(0xffffffffu, on);
+  unsigned rot = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) rot |= ((bal >> (i * GL)) & 1u) << i;
+  if (rot == 0) return 0;
+  J s = J(0), tau = J(0), tg = J(0);
+  if constexpr (sizeof(J) == 4)
+    rotation_params(am, bm, g, s, tau, tg);
+  else if (on)
+    rotation_params(am, bm, g, s, tau, tg);
+  J si[K], ti[K], gi[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    si[i] = __shfl_sync(0xffffffffu, s, i * GL);
+    ti[i] = __shfl_sync(0xffffffffu, tau, i * GL);
+    gi[i] = __shfl_sync(0xffffffffu, tg, i * GL);
+  }
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int j = (i + SH) % K;
+    if ((rot >> i) & 1u) {  // warp-uniform
+      rotate_lane(x[i], y[j], si[i], ti[i]);
+      a[i] -= gi[i];
+      bn[j] += gi[i];
+      xs[i] = sweep;
+      ys[j] = sweep;
+    }
+  }
+  return rot;
+}
+
+// y-side mask of a step's rotations (pair i touches y[(i + SH) mod K])
+template <int K, int SH>
+__device__ __forceinline__ unsigned y_mask(unsigned rot) {
+  unsigned m = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    if ((rot >> i) & 1u) m |= 1u << ((i + SH) % K);
+  return m;
 }
 
 // One round on the 2b staged columns (local columns [0, b) = block I, [b, 2b) =
-// block J): norms refreshed, then the pairs inside each block (first round of a
-// sweep only) and all b x b cross pairs.  s_nrm / s_stamp hold the squared
-// norms and the sweep of each column's last rotation.  Returns the number of
-// rotations this warp applied (identical in every lane).
-template <typename J, int NV>
+// block J), by G = b / K warps, each holding K columns of each block in
+// registers:
+//   norms   squared norms of the staged columns, refreshed (resets the drift of
+//           the tracked values);
+//   intra   (first round of a sweep only) the pairs inside each block, by the
+//           circle method over its b columns: b - 1 sub-steps of b disjoint
+//           pairs, K of them per warp;
+//   cross   all b x b cross pairs: warp w keeps columns [wK, wK + K) of block I
+//           and, in sub-round s, takes the K columns of group (w + s) mod G of
+//           block J; the K x K pairs of a meeting run as K steps of K disjoint
+//           pairs (x_i with y_{(i + step) mod K}).
+// Each column thus crosses shared memory once per K pairs instead of once per
+// pair, and each step has K independent reduction chains in flight.  s_nrm /
+// s_stamp hold the squared norms and the sweep of each column's last rotation
+// (stamps of block I at s_stamp[0, b), of block J at s_stamp[32, 32 + b)).
+// Returns the number of rotations this warp applied (identical in every lane).
+template <typename J, int NV, int K>
 __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int b, int rp, int t, int sweep,
-                                             J tol2, J tiny, int lane, int wid, int nw) {
-  constexpr int E = NV * Vec<J>::W;
+                                             J tol2, J tiny, int lane, int wid) {
+  const int G = b / K;  // warps doing pair work (== warps in the block)
+  auto col = [&](int c) { return sm + (int64_t)c * rp; };
+  auto sidx = [&](int c) { return c < b ? c : 32 + (c - b); };
   // a pair needs a check unless neither column has rotated since the previous sweep
   // (it was then verified orthogonal and has not changed since)
-  auto needs = [&](int p, int q) { return sweep == 0 || s_stamp[p] >= sweep - 1 || s_stamp[q] >= sweep - 1; };
-  // fresh squared norms of the staged columns (resets the drift of the tracked values)
-  for (int c = wid; c < 2 * b; c += nw) {
-    J x[E];
-    load_col<J, NV>(sm + (int64_t)c * rp, x, lane);
-    const J a = col_norm2<J, E>(x);
-    if (lane == 0) s_nrm[c] = a;
+  auto fresh = [&](int st) { return sweep == 0 || st >= sweep - 1; };
+  // fresh squared norms, K columns per warp at a time
+  for (int c0 = wid * K; c0 < 2 * b; c0 += G * K) {
+    Col<J, NV> x[K];
+    J nr[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) x[i].load(col(c0 + i), lane);
+#pragma unroll
+    for (int i = 0; i < K; ++i) nr[i] = dot_lane(x[i], x[i]);
+    const J t = warp_sum_spread<J, K>(nr, lane);
+    if ((lane & (32 / K - 1)) == 0) s_nrm[c0 + lane / (32 / K)] = t;
   }
   __syncthreads();
   int rot = 0;
   if (t == 0) {
-    // pairs inside each block, once per sweep (circle method over b slots, b even)
     const int hb = b / 2;
-    for (int s = 0; s < b - 1; ++s) {
-      for (int q = wid; q < b; q += nw) {
-        const int blk = q / hb, i = q % hb;
-        const int p0 = blk * b + circle_pos(i, s, b), p1 = blk * b + circle_pos(b - 1 - i, s, b);
-        if (!needs(p0, p1)) continue;
-        J* cp = sm + (int64_t)p0 * rp;
-        J* cq = sm + (int64_t)p1 * rp;
-        J x[E], y[E];
-        load_col<J, NV>(cp, x, lane);
-        load_col<J, NV>(cq, y, lane);
-        J a = s_nrm[p0], bb = s_nrm[p1];
-        if (rotate_regs<J, E>(x, y, a, bb, tol2, tiny)) {
-          store_col<J, NV>(cp, x, lane);
-          store_col<J, NV>(cq, y, lane);
+    for (int st = 0; st < b - 1; ++st) {
+      Col<J, NV> x[K], y[K];
+      J a[K], bn[K];
+      int xs[K], ys[K], p0[K], p1[K];
+      unsigned act = 0;
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int q = wid * K + i;  // pair q of this sub-step: block q / hb, slot q mod hb
+        const int blk = q >= hb ? 1 : 0, k = q - blk * hb;
+        p0[i] = blk * b + circle_pos(k, st, b);
+        p1[i] = blk * b + circle_pos(b - 1 - k, st, b);
+        x[i].load(col(p0[i]), lane);
+        y[i].load(col(p1[i]), lane);
+        a[i] = s_nrm[p0[i]];
+        bn[i] = s_nrm[p1[i]];
+        xs[i] = s_stamp[sidx(p0[i])];
+        ys[i] = s_stamp[sidx(p1[i])];
+        act |= (fresh(xs[i]) || fresh(ys[i])) ? (1u << i) : 0u;
+      }
+      const unsigned r = step_pairs<J, NV, K, 0>(x, y, a, bn, xs, ys, act, sweep, tol2, tiny, lane);
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        if ((r >> i) & 1u) {
+          x[i].store(col(p0[i]), lane);
+          y[i].store(col(p1[i]), lane);
           if (lane == 0) {
-            s_nrm[p0] = a;
-            s_nrm[p1] = bb;
-            s_stamp[p0] = sweep;
-            s_stamp[p1] = sweep;
+            s_nrm[p0[i]] = a[i];
+            s_nrm[p1[i]] = bn[i];
+            s_stamp[sidx(p0[i])] = sweep;
+            s_stamp[sidx(p1[i])] = sweep;
           }
           ++rot;
         }
@@ -298,89 +406,179 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
       __syncthreads();
     }
   }
-  // all b x b cross pairs: in sub-round s warp q pairs column q of block I with
-  // column (q + s) mod b of block J; warp q keeps its block-I column in registers
-  if (b <= nw) {
-    J x[E];
-    J* cx = sm + (int64_t)wid * rp;
-    J a = J(0);
-    if (wid < b) {
-      load_col<J, NV>(cx, x, lane);
-      a = s_nrm[wid];
+  {
+    Col<J, NV> x[K];
+    J a[K];
+    int xs[K];
+    const int xc = wid * K;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      x[i].load(col(xc + i), lane);
+      a[i] = s_nrm[xc + i];
+      xs[i] = s_stamp[sidx(xc + i)];
     }
-    bool xdirty = false;
-    for (int s = 0; s < b; ++s) {
-      if (wid < b) {
-        const int qy = b + (wid + s) % b;
-        if (needs(wid, qy)) {
-          J* cy = sm + (int64_t)qy * rp;
-          J y[E];
-          load_col<J, NV>(cy, y, lane);
-          J bb = s_nrm[qy];
-          if (rotate_regs<J, E>(x, y, a, bb, tol2, tiny)) {
-            store_col<J, NV>(cy, y, lane);
-            if (lane == 0) {
-              s_nrm[qy] = bb;
-              s_stamp[qy] = sweep;
-              s_stamp[wid] = sweep;
-            }
-            xdirty = true;
-            ++rot;
-          }
-        }
+    unsigned xdirty = 0;
+    int v = wid;
+    for (int s = 0; s < G; ++s) {
+      Col<J, NV> y[K];
+      J bn[K];
+      int ys[K];
+      const int yc = b + v * K;
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        bn[i] = s_nrm[yc + i];
+        ys[i] = s_stamp[sidx(yc + i)];
       }
-      __syncthreads();
-    }
-    if (wid < b && xdirty) {
-      store_col<J, NV>(cx, x, lane);
-      if (lane == 0) s_nrm[wid] = a;
-    }
-  } else {
-    // more pairs than warps: each warp takes several pairs per sub-round
-    for (int s = 0; s < b; ++s) {
-      for (int q = wid; q < b; q += nw) {
-        const int qy = b + (q + s) % b;
-        if (!needs(q, qy)) continue;
-        J* cx = sm + (int64_t)q * rp;
-        J* cy = sm + (int64_t)qy * rp;
-        J x[E], y[E];
-        load_col<J, NV>(cx, x, lane);
-        load_col<J, NV>(cy, y, lane);
-        J a = s_nrm[q], bb = s_nrm[qy];
-        if (rotate_regs<J, E>(x, y, a, bb, tol2, tiny)) {
-          store_col<J, NV>(cx, x, lane);
-          store_col<J, NV>(cy, y, lane);
+      unsigned ydirty = 0;
+      bool any = false;
+#pragma unroll
+      for (int i = 0; i < K; ++i) any = any || fresh(xs[i]) || fresh(ys[i]);
+      if (any)
+#pragma unroll
+        for (int i = 0; i < K; ++i) y[i].load(col(yc + i), lane);
+      auto act_mask = [&](int sh) {
+        unsigned m = 0;
+#pragma unroll
+        for (int i = 0; i < K; ++i) m |= (fresh(xs[i]) || fresh(ys[(i + sh) % K])) ? (1u << i) : 0u;
+        return m;
+      };
+      unsigned r = 0;
+      if (any) r = step_pairs<J, NV, K, 0>(x, y, a, bn, xs, ys, act_mask(0), sweep, tol2, tiny, lane);
+      xdirty |= r;
+      ydirty |= y_mask<K, 0>(r);
+      rot += __popc(r);
+      if (K > 1) {
+        r = any ? step_pairs<J, NV, K, 1 % K>(x, y, a, bn, xs, ys, act_mask(1 % K), sweep, tol2, tiny, lane) : 0u;
+        xdirty |= r;
+        ydirty |= y_mask<K, 1 % K>(r);
+        rot += __popc(r);
+      }
+      if (K > 2) {
+        r = any ? step_pairs<J, NV, K, 2 % K>(x, y, a, bn, xs, ys, act_mask(2 % K), sweep, tol2, tiny, lane) : 0u;
+        xdirty |= r;
+        ydirty |= y_mask<K, 2 % K>(r);
+        rot += __popc(r);
+        r = any ? step_pairs<J, NV, K, 3 % K>(x, y, a, bn, xs, ys, act_mask(3 % K), sweep, tol2, tiny, lane) : 0u;
+        xdirty |= r;
+        ydirty |= y_mask<K, 3 % K>(r);
+        rot += __popc(r);
+      }
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        if ((ydirty >> i) & 1u) {
+          y[i].store(col(yc + i), lane);
           if (lane == 0) {
-            s_nrm[q] = a;
-            s_nrm[qy] = bb;
-            s_stamp[q] = sweep;
-            s_stamp[qy] = sweep;
+            s_nrm[yc + i] = bn[i];
+            s_stamp[sidx(yc + i)] = ys[i];
           }
-          ++rot;
         }
       }
-      __syncthreads();
+      __syncthreads();  // the next holder of these columns loads them in the next sub-round
+      v = v + 1 == G ? 0 : v + 1;
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      if ((xdirty >> i) & 1u) {
+        x[i].store(col(xc + i), lane);
+        if (lane == 0) {
+          s_nrm[xc + i] = a[i];
+          s_stamp[sidx(xc + i)] = xs[i];
+        }
+      }
     }
   }
   __syncthreads();
   return rot;
 }
 
-// copy nvec 16-byte vectors (cooperatively over the CTA)
+// copy nvec 16-byte vectors (cooperatively over the CTA), eight loads in flight
+// per thread
 template <typename V>
 __device__ __forceinline__ void copy_vecs(V* dst, const V* src, int nvec, int tid, int nthr) {
-  for (int e = tid; e < nvec; e += nthr) dst[e] = src[e];
+  int e = tid;
+  for (; e + 7 * nthr < nvec; e += 8 * nthr) {
+    V v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = src[e + k * nthr];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dst[e + k * nthr] = v[k];
+  }
+  for (; e < nvec; e += nthr) dst[e] = src[e];
 }
 
+// ---- cluster shared-memory transfer primitives (PTX) ----------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for phase `parity` of a local mbarrier: false once ~2^31 cycles
+// (about a second) have passed without completion
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+// bulk copy of `bytes` (multiple of 16) from this CTA's shared memory to shared
+// memory of a CTA of the cluster; completion is signalled on that CTA's mbarrier
+__device__ __forceinline__ void bulk_push(uint32_t dst_cluster, const void* src, uint32_t bytes,
+                                          uint32_t mbar_cluster) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst_cluster),
+      "r"(smem_addr(src)), "r"(bytes), "r"(mbar_cluster)
+      : "memory");
+}
+// make this thread's generic-proxy shared-memory writes visible to the async proxy
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Block exchange between rounds.
 // DSM = true: the blocks stay in shared memory (two buffers) and move between
-// neighbouring CTAs of the cluster by remote shared-memory reads after each
-// cluster barrier.  Under the circle method the block at slot p >= 1 in round
-// t + 1 is the block at slot 1 + (p mod (2C - 1)) in round t (slot 0 is
-// fixed); slot s < C belongs to CTA s as its first block, slot s >= C to CTA
-// 2C - 1 - s as its second.  DSM = false: blocks go back to global memory
-// (L2) between rounds (used when two buffers do not fit).
+// CTAs of the cluster.  Under the circle method the block at slot q >= 1 in
+// round t moves to slot q - 1 in round t + 1 (slot 1 wraps to slot 2C - 1;
+// slot 0 is fixed); slot s < C belongs to CTA s as its first block, slot s >= C
+// to CTA 2C - 1 - s as its second.  After a round every CTA pushes its two
+// blocks (and their stamps) with bulk asynchronous copies straight into the
+// other buffer of their next holders, where the copies complete on that
+// buffer's mbarrier; one cluster barrier before the pushes guarantees that
+// every destination buffer has been consumed.  DSM = false: blocks go back to
+// global memory (L2) between rounds (used when two buffers do not fit).
+//
+// Stamps: s_stamp[buffer][half * 32 + c] for column c of block `half` (b <= 32),
+// so that each block's stamps are one 128-byte transfer.
+// columns per warp and block in the register-blocked rounds (K) and the largest
+// block (K columns per warp, b <= 32): four FP32 columns of up to 512 rows per
+// warp (8 columns x 16 registers in flight); two for longer FP32 columns and
+// for FP64
+template <typename J, int NV>
+struct PairK {
+  static constexpr int K = (sizeof(J) == 4 && NV <= 4) ? 4 : 2;
+  static constexpr int kMaxThreads = 32 * (32 / K);
+};
+
 template <typename J, int NV, bool DSM>
-__global__ void __launch_bounds__(512) jacobi_kernel(const __grid_constant__ JacobiBatch batch, double tol,
+__global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const __grid_constant__ JacobiBatch batch, double tol,
                                                       int max_sweeps) {
   using V = typename Vec<J>::T;
   cg::cluster_group cluster = cg::this_cluster();
@@ -391,18 +589,22 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const __grid_constant__ Jac
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_rot;
   __shared__ int s_cnt[2];
+  __shared__ int s_abort[2];
   __shared__ int s_total;
+  __shared__ int s_stop;
   __shared__ double s_tiny;
-  __shared__ J s_nrm[64];           // squared norms of the 2b staged columns
-  __shared__ int s_stamp[2][64];    // sweep in which each staged column last rotated (per buffer)
+  __shared__ J s_nrm[64];                       // squared norms of the 2b staged columns
+  __shared__ __align__(16) int s_stamp[2][64];  // sweep of each staged column's last rotation (per buffer)
+  __shared__ __align__(8) uint64_t s_full[2];   // per buffer: the incoming blocks have landed
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int nthr = blockDim.x, nw = nthr >> 5;
+  const int nthr = blockDim.x;
   const int b = P.b, rp = P.rows_pad, nblk = 2 * C;  // rp == 32 * E
   J* W = (J*)P.W;
   int* stamp = P.stamp;
   J* buf0 = (J*)smem_raw;
   J* buf1 = buf0 + (DSM ? (int64_t)2 * b * rp : 0);
+  const uint32_t blk_bytes = (uint32_t)((size_t)b * rp * sizeof(J));
   if (wid == 0) {
     // deterministic: fixed lane assignment, fixed shuffle tree
     double f = 0.0;
@@ -411,17 +613,26 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const __grid_constant__ Jac
     if (lane == 0) {
       s_tiny = Eps<J>::u * Eps<J>::u * f;
       s_cnt[0] = s_cnt[1] = 0;
+      s_abort[0] = s_abort[1] = 0;
     }
   }
   const int nvec = b * rp / Vec<J>::W;  // vectors per block
   int cur = 0;
+  uint32_t phase[2] = {0u, 0u};
+  bool aborted = false;
   if (DSM) {
     // initial blocks of round 0 from global memory
     const int bI = circle_pos(crank, 0, nblk), bJ = circle_pos(nblk - 1 - crank, 0, nblk);
     copy_vecs(reinterpret_cast<V*>(buf0), reinterpret_cast<const V*>(W + (int64_t)bI * b * rp), nvec, tid, nthr);
     copy_vecs(reinterpret_cast<V*>(buf0 + (int64_t)b * rp), reinterpret_cast<const V*>(W + (int64_t)bJ * b * rp),
               nvec, tid, nthr);
-    for (int c = tid; c < 2 * b; c += nthr) s_stamp[0][c] = -10;
+    for (int c = tid; c < 64; c += nthr) s_stamp[0][c] = -10;
+    if (tid == 0) {
+      mbar_init(&s_full[0], 1);
+      mbar_init(&s_full[1], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cluster.sync();  // every CTA's barriers are initialised before any push targets them
   }
   __syncthreads();
   const J tiny = (J)s_tiny;
@@ -435,18 +646,18 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const __grid_constant__ Jac
       const int bI = circle_pos(crank, t, nblk);
       const int bJ = circle_pos(nblk - 1 - crank, t, nblk);
       J* sm = (DSM && cur) ? buf1 : buf0;
+      int* st = s_stamp[DSM ? cur : 0];
       if (!DSM) {
         copy_vecs(reinterpret_cast<V*>(sm), reinterpret_cast<const V*>(W + (int64_t)bI * b * rp), nvec, tid, nthr);
         copy_vecs(reinterpret_cast<V*>(sm + (int64_t)b * rp), reinterpret_cast<const V*>(W + (int64_t)bJ * b * rp),
                   nvec, tid, nthr);
         for (int c = tid; c < 2 * b; c += nthr) {
           const int gc = (c < b ? bI * b + c : bJ * b + (c - b));
-          s_stamp[0][c] = sweep == 0 ? -10 : stamp[gc];
+          st[c < b ? c : 32 + (c - b)] = sweep == 0 ? -10 : stamp[gc];
         }
         __syncthreads();
       }
-      const int rot = process_round<J, NV>(sm, s_nrm, s_stamp[DSM ? cur : 0], b, rp, t, sweep, tol2, tiny, lane,
-                                           wid, nw);
+      const int rot = process_round<J, NV, PairK<J, NV>::K>(sm, s_nrm, st, b, rp, t, sweep, tol2, tiny, lane, wid);
       if (lane == 0 && rot) atomicAdd(&s_rot, rot);
       last_t = t;
       if (!DSM) {
@@ -455,49 +666,65 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const __grid_constant__ Jac
                   nvec, tid, nthr);
         for (int c = tid; c < 2 * b; c += nthr) {
           const int gc = (c < b ? bI * b + c : bJ * b + (c - b));
-          stamp[gc] = s_stamp[0][c];
+          stamp[gc] = st[c < b ? c : 32 + (c - b)];
         }
         // the cluster barrier's arrive (release) / wait (acquire) order these global
         // write-backs before any CTA of the cluster loads the blocks in the next round
         cluster.sync();
       } else {
-        cluster.sync();  // every CTA's blocks of this round are final
-        // pull the next round's two blocks (and their stamps) from their current holders
-        J* nxt = cur ? buf0 : buf1;
-        int* nst = s_stamp[cur ^ 1];
-        for (int half = 0; half < 2; ++half) {
-          const int slot = half == 0 ? crank : nblk - 1 - crank;
-          const int src_slot = slot == 0 ? 0 : 1 + (slot % (nblk - 1));
-          const int src_cta = src_slot < C ? src_slot : nblk - 1 - src_slot;
-          const int src_half = src_slot < C ? 0 : 1;
-          const J* rbuf = cluster.map_shared_rank(sm, src_cta) + (int64_t)src_half * b * rp;
-          const int* rst = cluster.map_shared_rank(s_stamp[cur], src_cta) + src_half * b;
-          copy_vecs(reinterpret_cast<V*>(nxt + (int64_t)half * b * rp), reinterpret_cast<const V*>(rbuf), nvec, tid,
-                    nthr);
-          for (int c = tid; c < b; c += nthr) nst[half * b + c] = rst[c];
+        const int nxt = cur ^ 1;
+        fence_proxy_async_smem();  // this round's rotations, visible to the bulk copies
+        cluster.sync();            // every CTA has finished this round: all destination buffers are free
+        if (tid == 0) {
+          mbar_arrive_expect_tx(&s_full[nxt], 2u * (blk_bytes + 128u));
+          J* dst_buf = nxt ? buf1 : buf0;
+          for (int half = 0; half < 2; ++half) {
+            const int slot = half == 0 ? crank : nblk - 1 - crank;
+            const int to = slot == 0 ? 0 : (slot >= 2 ? slot - 1 : nblk - 1);
+            const int to_cta = to < C ? to : nblk - 1 - to;
+            const int to_half = to < C ? 0 : 1;
+            const uint32_t mbar = cluster_addr(smem_addr(&s_full[nxt]), to_cta);
+            bulk_push(cluster_addr(smem_addr(dst_buf + (int64_t)to_half * b * rp), to_cta),
+                      sm + (int64_t)half * b * rp, blk_bytes, mbar);
+            bulk_push(cluster_addr(smem_addr(&s_stamp[nxt][to_half * 32]), to_cta), &s_stamp[cur][half * 32], 128u,
+                      mbar);
+          }
         }
-        cur ^= 1;
+        if (!aborted && !mbar_wait_bounded(&s_full[nxt], phase[nxt])) {
+          aborted = true;
+          s_abort[0] = 1;  // benign race: every writer stores 1
+        }
+        phase[nxt] ^= 1u;
+        cur = nxt;
         __syncthreads();
       }
     }
     if (tid == 0) s_cnt[sweep & 1] = s_rot;
     cluster.sync();
     if (tid == 0) {
-      int total = 0;
-      for (int q = 0; q < C; ++q) total += *cluster.map_shared_rank(&s_cnt[sweep & 1], q);
+      int total = 0, abort_any = 0;
+      for (int q = 0; q < C; ++q) {
+        total += *cluster.map_shared_rank(&s_cnt[sweep & 1], q);
+        abort_any |= *cluster.map_shared_rank(&s_abort[0], q);
+      }
       s_total = total;
+      s_stop = abort_any;
       // diagnostics: rotations applied in each sweep
       if (crank == 0 && P.sweeps_out && sweep < kSweepLog) P.sweeps_out[1 + sweep] = total;
     }
     __syncthreads();
+    if (s_stop) {  // a transfer never completed: give up with the status set
+      if (tid == 0) report(BKFAC_ETIMEOUT);
+      break;
+    }
     if (s_total == 0) {  // identical in every CTA of the cluster
       converged = true;
       break;
     }
   }
-  if (DSM) {
-    // write the final blocks back: after the last round's pull, buffer `cur` holds the
-    // blocks of the round after last_t
+  if (DSM && !s_stop) {
+    // write the final blocks back: after the last round's exchange, buffer `cur`
+    // holds the blocks of the round after last_t
     const int tn = last_t + 1;
     const int bI = circle_pos(crank, tn, nblk), bJ = circle_pos(nblk - 1 - crank, tn, nblk);
     const J* sm = cur ? buf1 : buf0;
@@ -507,14 +734,16 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const __grid_constant__ Jac
   }
   if (crank == 0 && tid == 0) {
     if (P.sweeps_out) *P.sweeps_out = converged ? sweep + 1 : sweep;
-    if (!converged) report(BKFAC_ENOCONV);
+    if (!converged && !s_stop) report(BKFAC_ENOCONV);
   }
-  cluster.sync();  // keep every CTA's shared memory alive until all remote reads are done
+  cluster.sync();  // keep every CTA's shared memory alive until all remote accesses are done
 }
 
 template <typename J, int NV, bool DSM>
 int launch_typed(const JacobiBatch& batch, int nprob, int C, int b, size_t smem, double tol, int max_sweeps,
                  cudaStream_t s) {
+  if (b % PairK<J, NV>::K != 0 || b / PairK<J, NV>::K * 32 > PairK<J, NV>::kMaxThreads)
+    return (int)cudaErrorInvalidValue;
   auto kfn = jacobi_kernel<J, NV, DSM>;
   // function attributes are set once per instantiation (the call can stall the host)
   static std::atomic<int> configured{0};
@@ -528,7 +757,7 @@ int launch_typed(const JacobiBatch& batch, int nprob, int C, int b, size_t smem,
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nprob * C), 1, 1);
-  cfg.blockDim = dim3((unsigned)(32 * std::min(b, 16)), 1, 1);
+  cfg.blockDim = dim3((unsigned)(32 * (b / PairK<J, NV>::K)), 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -570,13 +799,16 @@ void jacobi_plan_with(int rows, int cols, DType j_t, int b_max, int* C_out, int*
                       int* cols_pad) {
   const int rp = rows_pad_for(std::max(rows, 1), j_t);
   const size_t es = j_t == DT_F64 ? 8 : 4;
+  // block widths are multiples of the register-blocking width K (see PairK)
+  const int nv = rp / (32 * (j_t == DT_F64 ? 2 : 4));
+  const int K = (j_t == DT_F32 && nv <= 4) ? 4 : 2;
   const size_t smem_cap = 200 * 1024;
   int C = 16, b = 32;
   // smallest cluster whose blocks are at most b_max columns wide and fit in shared
   // memory; fall back to wider blocks when 16 CTAs are not enough
   bool found = false;
   for (int c : {1, 2, 4, 8, 16}) {
-    const int bb = (int)round_up(ceil_div(std::max(cols, 2), 2 * c), 2);
+    const int bb = (int)round_up(ceil_div(std::max(cols, 2), 2 * c), K);
     if (bb <= b_max && (size_t)2 * bb * rp * es <= smem_cap) {
       C = c;
       b = bb;
@@ -586,7 +818,7 @@ void jacobi_plan_with(int rows, int cols, DType j_t, int b_max, int* C_out, int*
   }
   if (!found) {
     C = 16;
-    b = (int)round_up(ceil_div(std::max(cols, 2), 32), 2);
+    b = (int)round_up(ceil_div(std::max(cols, 2), 32), K);
   }
   *C_out = C;
   *b_out = b;
@@ -602,7 +834,9 @@ void jacobi_plan(int rows, int cols, DType j_t, int* C_out, int* b_out, int* row
 
 int launch_jacobi(const JacobiProblem* probs, int nprob, int C, DType j_t, double tol, int max_sweeps,
                   cudaStream_t s) {
-  int b = 0, dsm = 0;
+  // block exchange over distributed shared memory unless the tuning table says
+  // otherwise (it is used only where two buffers fit)
+  int b = 0, dsm = 1;
   if (nprob > 0) tune_lookup(probs[0].rows, probs[0].cols, j_t, &b, &dsm);
   return launch_jacobi_mode(probs, nprob, C, j_t, tol, max_sweeps, dsm != 0, s);
 }
@@ -626,8 +860,8 @@ int launch_jacobi_mode(const JacobiProblem* probs, int nprob, int C, DType j_t, 
     smem = std::max(smem, jacobi_smem_bytes(probs[i].b, probs[i].rows_pad, j_t));
   }
   if (b < 2 || b > 32 || (b & 1) || smem > 200 * 1024) return (int)cudaErrorInvalidValue;
-  // block exchange between rounds: through L2 by default; over distributed shared
-  // memory (two buffers) when the tuning table asks for it and the buffers fit
+  // block exchange between rounds: over distributed shared memory (two buffers)
+  // when asked for and the buffers fit, else through L2
   const bool dsm = want_dsm && 2 * smem <= 200 * 1024;
   if (j_t == DT_F64)
     return dsm ? launch_nv<double, true>(batch, nprob, C, b, rp, 2 * smem, tol, max_sweeps, s)
