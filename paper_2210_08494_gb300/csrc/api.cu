@@ -78,7 +78,8 @@ struct UpdatePlan {
   int64_t ldq, ldm, ldv;
   int C, b, rows_pad, cols_pad;  // Jacobi plan of this call
   int rows_cap, cols_cap;        // capacity of L
-  size_t o_scale, o_M, o_part, o_P, o_Q1, o_Q, o_G, o_R1, o_R2, o_Rinv, o_L, o_cn, o_lam, o_V, o_Un, o_sw, o_st;
+  size_t o_scale, o_M, o_part, o_P, o_Q1, o_Q, o_G, o_R1, o_R2, o_Rinv, o_L, o_cn, o_lam, o_V, o_Un, o_sw, o_st,
+      o_flag;
   size_t part_bytes;
   size_t total;
 };
@@ -109,7 +110,7 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
     int C2, b2, rp2, cp2;
     jacobi_plan(f->d, f->r + n, p.pr.jt, &C2, &b2, &rp2, &cp2);
     rows_cap = rp2;
-    cols_cap = (int)round_up(f->r + n, 32) + 64;
+    cols_cap = (int)round_up(f->r + n, 32) + 128;
     p.o_L = L.add((size_t)rows_cap * cols_cap * jes);
     p.o_cn = L.add((size_t)cols_cap * 8);
     p.o_lam = L.add((size_t)cols_cap * 8);
@@ -125,7 +126,9 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
     int C2, b2, rp2, cp2;
     jacobi_plan(Nmax, Nmax, p.pr.jt, &C2, &b2, &rp2, &cp2);
     rows_cap = rp2;
-    cols_cap = (int)round_up(Nmax, 32) + 64;
+    // the Jacobi pads the columns to 2 C b with b a multiple of the register
+    // blocking width K: at most 2 C K <= 128 columns beyond N
+    cols_cap = (int)round_up(Nmax, 32) + 128;
     p.o_scale = L.add(8);
     p.o_M = L.add((size_t)p.ldm * n * es);
     const size_t part = std::max(partial_bytes(kmax, n, f->d, aes), partial_bytes(n, n, f->d, 8));
@@ -145,6 +148,7 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
     p.o_Un = L.add((size_t)p.ldq * f->r * es);
     p.o_sw = L.add(256);
     p.o_st = L.add((size_t)cols_cap * 4);
+    p.o_flag = L.add(16);
   }
   p.rows_cap = rows_cap;
   p.cols_cap = cols_cap;
@@ -174,7 +178,7 @@ ReorthPlan plan_reorth(const bkfac_factor* f, int k) {
   int C2, b2, rp2, cp2;
   jacobi_plan(kmax, kmax, p.pr.jt, &C2, &b2, &rp2, &cp2);
   p.rows_cap = rp2;
-  p.cols_cap = (int)round_up(kmax, 32) + 64;
+  p.cols_cap = (int)round_up(kmax, 32) + 128;
   Layout L;
   p.o_part = L.add(partial_bytes(kmax, kmax, f->d, 8));
   p.o_G = L.add((size_t)kmax * kmax * 8);
@@ -250,9 +254,11 @@ P* at(void* ws, size_t off) {
   } while (0)
 
 // Cholesky: the cluster kernel when n fits it, else the single-CTA kernel
+// near_out (may be null) receives whether the near-identity shortcut was taken
 int run_chol(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
-             cudaStream_t s) {
-  if (chol_cluster_size(n) > 0) return launch_chol_cluster(Gm, n, R, thr_rel, scale, near_tol, s);
+             int* near_out, cudaStream_t s) {
+  if (chol_cluster_size(n) > 0) return launch_chol_cluster(Gm, n, R, thr_rel, scale, near_tol, near_out, s);
+  if (near_out != nullptr && cudaMemsetAsync(near_out, 0, sizeof(int), s) != cudaSuccess) return BKFAC_ECUDA;
   return launch_chol(Gm, n, R, thr_rel, scale, s);
 }
 
@@ -283,7 +289,12 @@ int run_gram(const void* A, int64_t lda, int d, int n, Prec pr, double* G, void*
   g.C = G;
   g.ldc = n;
   g.sym = true;
-  g.splits = std::max(2, gemm_pick_splits(n, n, d, 152));
+  // only the upper tiles of the symmetric output are computed: split K until about
+  // two CTAs per SM are busy (at most 32 partials, at least 128 rows of K each)
+  const int64_t tiles = ceil_div(n, 64), active = tiles * (tiles + 1) / 2;
+  int64_t splits = ceil_div(2 * 152, active);
+  splits = std::min<int64_t>(std::min<int64_t>(splits, 32), std::max<int64_t>(1, d / 128));
+  g.splits = (int)std::max<int64_t>(2, splits);
   g.partial = part;
   // FP32 data: FP64-accurate Gram on the FP32 pipes (compensated); FP64 data: DFMA
   if (pr.t == DT_F32) return gram_run_comp(g, s);
@@ -426,12 +437,13 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   const double thr1 = pr.bf16 ? (2.0 * ue) * (2.0 * ue) : (64.0 * ue) * (64.0 * ue);
   const double thr2 = (64.0 * pr.u_t) * (64.0 * pr.u_t);
   PHASE(PH_GRAM, run_gram(Pp, ldp, d, n, pr, Gm, part, s));
-  PHASE(PH_CHOL, run_chol(Gm, n, R1, thr1, scale, 0.0, s));
-  PHASE(PH_TRINV, launch_trinv(R1, n, Rinv, pr.t, s));
+  PHASE(PH_CHOL, run_chol(Gm, n, R1, thr1, scale, 0.0, nullptr, s));
+  PHASE(PH_TRINV, launch_trinv(R1, n, Rinv, pr.t, nullptr, s));
   PHASE(PH_TRMM, run_trmm(Pp, ldp, d, n, Rinv, pr, Q1, p.ldq, part, p.part_bytes, s));
   PHASE(PH_GRAM, run_gram(Q1, p.ldq, d, n, pr, Gm, part, s));
-  PHASE(PH_CHOL, run_chol(Gm, n, R2, thr2, nullptr, near_identity_tol(pr), s));
-  PHASE(PH_TRINV, launch_trinv(R2, n, Rinv, pr.t, s));
+  int* near = at<int>(ws, p.o_flag);
+  PHASE(PH_CHOL, run_chol(Gm, n, R2, thr2, nullptr, near_identity_tol(pr), near, s));
+  PHASE(PH_TRINV, launch_trinv(R2, n, Rinv, pr.t, near, s));
   PHASE(PH_TRMM, run_trmm(Q1, p.ldq, d, n, Rinv, pr, Q, p.ldq, part, p.part_bytes, s));
   // core factor L and its Jacobi eigensolve
   CoreArgs ca;
@@ -614,8 +626,8 @@ int bkfac_reorth(bkfac_factor* f, void* ws, size_t ws_bytes, bkfac_stream_t stre
   void* Rinv = at<void>(ws, cap.o_Rinv);
   void* Q = at<void>(ws, cap.o_Q);
   BK_TRY(run_gram(f->U, f->ldu, d, k, pr, Gm, at<void>(ws, cap.o_part), s));
-  BK_TRY(run_chol(Gm, k, R, (64.0 * pr.u_t) * (64.0 * pr.u_t), nullptr, 0.0, s));
-  BK_TRY(launch_trinv(R, k, Rinv, pr.t, s));
+  BK_TRY(run_chol(Gm, k, R, (64.0 * pr.u_t) * (64.0 * pr.u_t), nullptr, 0.0, nullptr, s));
+  BK_TRY(launch_trinv(R, k, Rinv, pr.t, nullptr, s));
   BK_TRY(run_trmm(f->U, f->ldu, d, k, Rinv, pr, Q, cap.ldq, nullptr, 0, s));
   void* Lm = at<void>(ws, cap.o_L);
   double* cn = at<double>(ws, cap.o_cn);

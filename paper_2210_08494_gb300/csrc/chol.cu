@@ -32,7 +32,8 @@ namespace {
 constexpr int CT = 512;
 
 __global__ void __launch_bounds__(CT) chol_cluster_kernel(const double* __restrict__ Gm, int n, double* R,
-                                                          double thr_rel, const double* scale, double near_tol) {
+                                                          double thr_rel, const double* scale, double near_tol,
+                                                          int* near_out) {
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int q = (int)cluster.block_rank();
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(CT) chol_cluster_kernel(const double* __restri
   }
   __syncthreads();
   const int s_near = s_flag[1];
+  if (near_out != nullptr && q == 0 && tid == 0) *near_out = s_near;
   if (s_near) {
     // R = I + Phi(E): row c of R holds E[c, i] for i > c and 1 + E[c, c] / 2 on the diagonal
     for (int jl = 0; jl < wq; ++jl) {
@@ -180,7 +182,7 @@ int chol_cluster_size(int n) {
 }
 
 int launch_chol_cluster(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
-                        cudaStream_t s) {
+                        int* near_out, cudaStream_t s) {
   if (n <= 0) return 0;
   const int C = chol_cluster_size(n);
   if (C == 0) return (int)cudaErrorInvalidValue;
@@ -206,7 +208,7 @@ int launch_chol_cluster(const double* Gm, int n, double* R, double thr_rel, cons
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, chol_cluster_kernel, Gm, n, R, thr_rel, scale, near_tol);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, chol_cluster_kernel, Gm, n, R, thr_rel, scale, near_tol, near_out);
   note_launches(1);
   return (int)e;
 }

@@ -93,6 +93,12 @@ int gemm_run(const GemmArgs& g, DType in_t, DType acc_t, DType out_t, cudaStream
 int gram_run_comp(const GemmArgs& g, cudaStream_t s);
 // suggested split count for a long-K product with small output
 int gemm_pick_splits(int M, int N, int K, int sm_count);
+// BF16-operand / FP32-accumulate product on the tensor cores (tc_gemm.cu), same
+// contract as gemm_run in mixed mode; split-K partials are summed by
+// splitk_reduce_f32 (gemm.cu) in a fixed order
+int tc_gemm_run(const GemmArgs& g, cudaStream_t s);
+bool tc_gemm_enabled();
+int splitk_reduce_f32(const GemmArgs& g, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Small dense kernels (small.cu)
@@ -103,12 +109,15 @@ int launch_colnorm_max(const void* X, int64_t ldx, int d, int n, DType t, double
 // pivot j dropped (row j of R zero) when s_j <= thr_rel * (*scale).  scale may be null (= 1).
 int launch_chol(const double* Gm, int n, double* R, double thr_rel, const double* scale, cudaStream_t s);
 // the same factorisation on a thread-block cluster (chol.cu); with near_tol > 0 and
-// max|G - I| <= near_tol the factor is I + (strict upper part + half diagonal of G - I)
+// max|G - I| <= near_tol the factor is I + (strict upper part + half diagonal of G - I);
+// near_out (may be null) receives 1 when that shortcut was taken, else 0
 int launch_chol_cluster(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
-                        cudaStream_t s);
+                        int* near_out, cudaStream_t s);
 int chol_cluster_size(int n);  // 0 when n is too large for the cluster kernel
-// inverse of the upper-triangular R (zero rows = dropped pivots -> zero rows/cols of Rinv)
-int launch_trinv(const double* R, int n, void* Rinv, DType t, cudaStream_t s);
+// inverse of the upper-triangular R (zero rows = dropped pivots -> zero rows/cols of Rinv);
+// when near (may be null) points to a nonzero flag, R = I + F is near identity and
+// Rinv = I - F (exact to O(|F|^2)) is written instead
+int launch_trinv(const double* R, int n, void* Rinv, DType t, const int* near, cudaStream_t s);
 
 struct CoreArgs {
   int k, n, N;            // old rank, batch width, core size N = k + n

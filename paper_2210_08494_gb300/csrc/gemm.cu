@@ -546,8 +546,19 @@ int gram_run_comp(const GemmArgs& g, cudaStream_t s) {
   return (int)cudaGetLastError();
 }
 
+int splitk_reduce_f32(const GemmArgs& g, cudaStream_t s) {
+  const int64_t total = (int64_t)g.M * g.N;
+  const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
+  splitk_reduce<float, float><<<blocks, 256, 0, s>>>(g);
+  note_launches(1);
+  return (int)cudaGetLastError();
+}
+
 int gemm_run(const GemmArgs& g, DType in_t, DType acc_t, DType out_t, cudaStream_t s) {
   if (in_t == DT_F64 && acc_t == DT_F64 && out_t == DT_F64) return run_typed<double, double, double>(g, s);
+  // mixed precision (BF16 operands, FP32 accumulation): the tensor cores
+  if (in_t == DT_F32 && acc_t == DT_F32 && out_t == DT_F32 && g.round_bf16 && !g.sym && tc_gemm_enabled())
+    return tc_gemm_run(g, s);
   if (in_t == DT_F32 && acc_t == DT_F32 && out_t == DT_F32) {
     if (large_ok(g)) {
       // enough CTAs for the GPU: split K when the output has few 128 x 128 tiles

@@ -159,6 +159,104 @@ __global__ void __launch_bounds__(1024) trinv_kernel(const double* __restrict__ 
   for (int i = lane; i < n; i += 32) out[i] = i <= j ? y[i] : T(0);
 }
 
+// Blocked inverse of the upper-triangular R for n <= 256 (at most 8 diagonal
+// blocks of 32): CTA jb computes block column jb of R^-1 (32 columns) as
+//   Y_B(jb) = D_jb^-1,  then for i = jb - 1, ..., 0:
+//   Y_B(i) = -D_i^-1 sum_{k = i+1..jb} R_ik Y_B(k),
+// organised as a block back-substitution: after Y_B(i) is final, every block
+// above it receives its update -R_{i', i} Y_B(i) (i' < i) at once, so the
+// sequential depth is the number of blocks, not n.  D_i^-1 (inverse of the
+// 32 x 32 diagonal block) is computed first, one warp per block, one lane per
+// column.  Dropped pivots (zero rows of R) give zero rows and columns.
+//
+// Near-identity pass (near != null and *near != 0, set by the Cholesky of the
+// second CholeskyQR pass): R = I + F with |F| tiny, R^-1 = I - F + O(|F|^2),
+// written directly.
+template <typename T>
+__global__ void __launch_bounds__(1024) trinv_blocked_kernel(const double* __restrict__ R, int n, T* Rinv,
+                                                             const int* near) {
+  extern __shared__ __align__(16) unsigned char tb_smem[];
+  const int jb = blockIdx.x;
+  const int nb = jb + 1;              // blocks 0..jb take part
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int j0 = 32 * jb;
+  if (near != nullptr && *near != 0) {
+    for (int c = wid; c < 32; c += 32) {
+      const int j = j0 + c;
+      if (j >= n) break;
+      for (int r = lane; r < n; r += 32) {
+        const double v = R[r + (int64_t)j * n];
+        Rinv[r + (int64_t)j * n] = (T)(r == j ? 2.0 - v : (r < j ? -v : 0.0));
+      }
+    }
+    return;
+  }
+  T* Dinv = (T*)tb_smem;            // nb blocks, 32 x 32 column-major each
+  T* Y = Dinv + nb * 1024;          // 32 nb rows x 32 columns, column-major (ld 32 nb)
+  T* P = Y + nb * 1024;             // panel R[0 : 32 i, 32 i : 32 i + 32], column-major (ld 32 i)
+  const int ldy = 32 * nb;
+  // ---- diagonal block inverses: warp i < nb inverts D_i, staged in the Y area
+  if (wid < nb) {
+    T* Ds = Y + wid * 1024;
+    const int o = 32 * wid;
+    for (int m = 0; m < 32; ++m) {
+      const int r = o + lane, c = o + m;
+      Ds[lane + 32 * m] = (r < n && c < n) ? (T)R[r + (int64_t)c * n] : (lane == m ? T(1) : T(0));
+    }
+    __syncwarp();
+    const T dll = Ds[lane + 32 * lane];
+    const T inv_mine = dll != T(0) ? T(1) / dll : T(0);
+    T x[32];
+#pragma unroll
+    for (int l = 31; l >= 0; --l) {
+      T acc = (l == lane) ? T(1) : T(0);
+#pragma unroll
+      for (int m = l + 1; m < 32; ++m) acc -= Ds[l + 32 * m] * x[m];
+      const T il = __shfl_sync(0xffffffffu, inv_mine, l);
+      x[l] = (l <= lane) ? acc * il : T(0);
+    }
+    __syncwarp();
+    T* Dw = Dinv + wid * 1024;
+#pragma unroll
+    for (int l = 0; l < 32; ++l) Dw[l + 32 * lane] = x[l];
+  }
+  __syncthreads();
+  // ---- Y = e_{j0 .. j0 + 31} restricted to rows [0, 32 nb); thread (row = lane + 32 k, col = wid)
+  const int c = wid;  // this warp's column of the block column
+  for (int r = lane; r < ldy; r += 32) Y[r + ldy * c] = (r == j0 + c) ? T(1) : T(0);
+  __syncthreads();
+  for (int i = jb; i >= 0; --i) {
+    // Y_B(i) <- D_i^-1 Y_B(i)
+    const T* Di = Dinv + i * 1024;
+    T v = T(0);
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) v += Di[lane + 32 * k] * Y[32 * i + k + ldy * c];
+    __syncthreads();
+    Y[32 * i + lane + ldy * c] = v;
+    if (i == 0) break;
+    // panel R[0 : 32 i, 32 i : 32 i + 32] into shared memory
+    const int pr = 32 * i;
+    for (int e = threadIdx.x; e < pr * 32; e += blockDim.x) {
+      const int r = e % pr, k = e / pr;
+      const int col = 32 * i + k;
+      P[e] = (col < n) ? (T)R[r + (int64_t)col * n] : T(0);
+    }
+    __syncthreads();
+    // Y_B(i') -= R_{i', i} Y_B(i) for every block i' < i
+    for (int r = lane; r < pr; r += 32) {
+      T acc = T(0);
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) acc += P[r + pr * k] * Y[32 * i + k + ldy * c];
+      Y[r + ldy * c] -= acc;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  const int j = j0 + c;
+  if (j < n)
+    for (int r = lane; r < n; r += 32) Rinv[r + (int64_t)j * n] = (r < ldy && r <= j) ? Y[r + ldy * c] : T(0);
+}
+
 // ---------------------------------------------------------------- core factor L
 // L = [[diag(sqrt(rho sigma)), sqrt(c) M], [0, sqrt(c) R2 R1]]  so that
 // L L^T = M_S of Eq. (7) with D <- rho diag(sigma), A <- sqrt(c) X, R = R2 R1.
@@ -398,12 +496,30 @@ void trinv_launch(const double* R, int n, T* Rinv, cudaStream_t s) {
     trinv_kernel<T, false><<<blocks, 1024, xs, s>>>(R, n, Rinv);
 }
 
-int launch_trinv(const double* R, int n, void* Rinv, DType t, cudaStream_t s) {
+template <typename T>
+void trinv_blocked_launch(const double* R, int n, T* Rinv, const int* near, cudaStream_t s) {
+  static std::atomic<int> configured{0};  // attribute set once (the call can stall the host)
+  if (!configured.load()) {
+    cudaFuncSetAttribute(trinv_blocked_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    configured.store(1);
+  }
+  const int nb = (int)ceil_div(n, 32);
+  const size_t smem = (size_t)3 * nb * 1024 * sizeof(T);
+  trinv_blocked_kernel<T><<<nb, 1024, smem, s>>>(R, n, Rinv, near);
+}
+
+int launch_trinv(const double* R, int n, void* Rinv, DType t, const int* near, cudaStream_t s) {
   if (n <= 0) return 0;
-  if (t == DT_F64)
+  if (n <= 256) {
+    if (t == DT_F64)
+      trinv_blocked_launch<double>(R, n, (double*)Rinv, near, s);
+    else
+      trinv_blocked_launch<float>(R, n, (float*)Rinv, near, s);
+  } else if (t == DT_F64) {
     trinv_launch<double>(R, n, (double*)Rinv, s);
-  else
+  } else {
     trinv_launch<float>(R, n, (float*)Rinv, s);
+  }
   note_launches(1);
   return (int)cudaGetLastError();
 }

@@ -1,0 +1,379 @@
+// tc_gemm.cu -- the tall-skinny products of the mixed-precision path on the
+// 5th-generation tensor cores (tcgen05): BF16 operands, FP32 accumulation in
+// tensor memory (TMEM).
+//
+// Same contract as the SIMT GEMM (common.cuh, GemmArgs): C[m, n] = alpha rs[m]
+// cs[n] sum_k A[m, k] B[k, n] + beta ds[n] D[m, n], A = [A0 | A1] and
+// B = [B0 ; B1] split along K, any of the four operand layouts, FP32 in memory.
+// Operands are rounded to BF16 (round to nearest even, the same rounding the
+// SIMT path applies in mixed mode) while they are staged into shared memory.
+//
+// Tile: 128 x 128 outputs per CTA (one tcgen05.mma.cta_group::1 of M = 128,
+// N = 128 per K step of 16), K staged 64 at a time in two shared-memory buffers.
+// Four warps convert and store the next K block while the tensor core works on
+// the current one; one thread issues the MMAs and commits them to the buffer's
+// mbarrier, which releases the buffer for reuse.  The accumulator lives in 128
+// TMEM columns; the epilogue reads it back with tcgen05.ld (warp w reads TMEM
+// lanes 32w .. 32w + 31, i.e. output rows), applies the scaling and writes C,
+// or a split-K partial that splitk_reduce sums in a fixed order.
+//
+// Shared-memory operand layout: K-major, no swizzle.  Each K step of 16 is a
+// 128 x 16 sub-tile (4 KB) built from 8 x 16-byte "core matrices" (8 rows of 8
+// BF16): core matrices adjacent in K are 128 bytes apart (leading byte offset),
+// 8-row groups 256 bytes apart (stride byte offset).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace bkfac {
+namespace {
+
+constexpr int TM = 128, TN = 128, TK = 64, TKS = 16;  // tile M, N, staged K, K per MMA
+constexpr int TC_THREADS = 128;
+constexpr int SUB_BYTES = TM * TKS * 2;         // one 128 x 16 BF16 sub-tile
+constexpr int STAGE_BYTES = 2 * (TK / TKS) * SUB_BYTES;  // A and B, 4 sub-tiles each
+constexpr int TMEM_COLS = 128;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading / stride byte offsets
+// (16-byte units), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait (about a second of clock cycles); false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// A[m, k] of the concatenated operand (zero outside)
+__device__ __forceinline__ float ld_a(const GemmArgs& g, int m, int k, int K) {
+  if (m >= g.M || k >= K) return 0.f;
+  const float* A = (const float*)g.A0;
+  int64_t lda = g.lda0;
+  if (k >= g.K0) {
+    A = (const float*)g.A1;
+    lda = g.lda1;
+    k -= g.K0;
+  }
+  return __ldg(g.a_kmaj ? A + (int64_t)m * lda + k : A + m + (int64_t)k * lda);
+}
+// B[k, n]: element (n, k) of the K-major view B^T
+__device__ __forceinline__ float ld_b(const GemmArgs& g, int n, int k, int K) {
+  if (n >= g.N || k >= K) return 0.f;
+  const float* B = (const float*)g.B0;
+  int64_t ldb = g.ldb0;
+  if (k >= g.K0) {
+    B = (const float*)g.B1;
+    ldb = g.ldb1;
+    k -= g.K0;
+  }
+  return __ldg(g.b_kmaj ? B + (int64_t)n * ldb + k : B + (int64_t)k * ldb + n);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// byte offset of element (row, k) (k in [0, 64)) of a staged 128 x 64 operand:
+// sub-tile k / 16, then core matrix (row / 8, (k mod 16) / 8), then row mod 8
+__device__ __forceinline__ uint32_t tile_off(int row, int k) {
+  return (uint32_t)((k >> 4) * SUB_BYTES + (row >> 3) * 256 + ((k >> 3) & 1) * 128 + (row & 7) * 16);
+}
+
+// Segment of the concatenated operand holding K index k (k < K), the element
+// pointer of (row, k), and whether 16-byte vector loads of 4 consecutive
+// elements along the contiguous index are legal there.
+struct Seg {
+  const float* p;
+  int64_t ld;
+  int k;  // K index within the segment
+  bool vec;
+};
+template <bool IS_A>
+__device__ __forceinline__ Seg seg_of(const GemmArgs& g, int k) {
+  const bool first = k < g.K0;
+  const float* p = (const float*)(IS_A ? (first ? g.A0 : g.A1) : (first ? g.B0 : g.B1));
+  const int64_t ld = IS_A ? (first ? g.lda0 : g.lda1) : (first ? g.ldb0 : g.ldb1);
+  Seg s;
+  s.p = p;
+  s.ld = ld;
+  s.k = first ? k : k - g.K0;
+  s.vec = ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) && ((ld & 3) == 0);
+  return s;
+}
+
+// Stage rows [r0, r0 + 128) x K block [k0, k0 + 64) of one operand into `dst`
+// (BF16, canonical layout); rows >= R (M or N) and K >= K read as zero.
+// `kmaj`: the operand's K index is contiguous in memory.  Work items are 8
+// consecutive K of one row (one 16-byte core-matrix row): K-contiguous operands
+// are read along K (8 lanes per 256-byte row segment, two 16-byte loads per
+// item), the others along rows (lanes over 4-row groups, one 16-byte load per
+// K).  Items that straddle an edge, the K0 seam or a misaligned start fall back
+// to element loads.
+template <bool IS_A>
+__device__ __forceinline__ void stage_operand(const GemmArgs& g, unsigned char* dst, int r0, int k0, int K, int tid) {
+  const bool kmaj = IS_A ? g.a_kmaj : g.b_kmaj;
+  const int R = IS_A ? g.M : g.N;
+  if (kmaj) {
+    for (int it = tid; it < TM * 8; it += TC_THREADS) {
+      const int row = it >> 3, kc = (it & 7) * 8;
+      const int gr = r0 + row, gk = k0 + kc;
+      float v[8];
+      const Seg sg = seg_of<IS_A>(g, min(gk, max(K - 1, 0)));
+      const bool fast = gr < R && gk + 8 <= K && (gk >= g.K0 || gk + 8 <= g.K0) && sg.vec && (sg.k & 3) == 0;
+      if (fast) {
+        const float4* q = reinterpret_cast<const float4*>(sg.p + (int64_t)gr * sg.ld + sg.k);
+        const float4 x0 = __ldg(q), x1 = __ldg(q + 1);
+        v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+        v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = IS_A ? ld_a(g, gr, gk + e, K) : ld_b(g, gr, gk + e, K);
+      }
+      uint4 q;
+      q.x = pack_bf16(v[0], v[1]);
+      q.y = pack_bf16(v[2], v[3]);
+      q.z = pack_bf16(v[4], v[5]);
+      q.w = pack_bf16(v[6], v[7]);
+      *reinterpret_cast<uint4*>(dst + tile_off(row, kc)) = q;
+    }
+  } else {
+    for (int it = tid; it < (TM / 4) * 8; it += TC_THREADS) {
+      const int rq = (it & 31) * 4, kc = (it >> 5) * 8;
+      const int gr = r0 + rq, gk = k0 + kc;
+      float v[4][8];
+      const bool rows_in = gr + 4 <= R;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = gk + e;
+        bool done = false;
+        if (rows_in && k < K) {
+          const Seg sg = seg_of<IS_A>(g, k);
+          if (sg.vec) {  // r0 and rq are multiples of 4: the 4 rows form one aligned vector
+            const float4 x = __ldg(reinterpret_cast<const float4*>(sg.p + gr + (int64_t)sg.k * sg.ld));
+            v[0][e] = x.x; v[1][e] = x.y; v[2][e] = x.z; v[3][e] = x.w;
+            done = true;
+          }
+        }
+        if (!done)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) v[i][e] = IS_A ? ld_a(g, gr + i, k, K) : ld_b(g, gr + i, k, K);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        uint4 q;
+        q.x = pack_bf16(v[i][0], v[i][1]);
+        q.y = pack_bf16(v[i][2], v[i][3]);
+        q.z = pack_bf16(v[i][4], v[i][5]);
+        q.w = pack_bf16(v[i][6], v[i][7]);
+        *reinterpret_cast<uint4*>(dst + tile_off(rq + i, kc)) = q;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const GemmArgs g) {
+  extern __shared__ __align__(16) unsigned char tc_smem_raw[];  // only 16 bytes are guaranteed
+  __shared__ __align__(8) uint64_t s_mma_done[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int K = g.K0 + g.K1;
+  const int kb = blockIdx.z * g.k_chunk;
+  const int ke = min(K, kb + g.k_chunk);
+  const int nk = (ke - kb + TK - 1) / TK;
+  // operand tiles on a 1024-byte boundary of the shared window, computed at run
+  // time: the dynamic region starts right after the static variables (measured:
+  // 32 bytes past a boundary), and the tensor core reads a no-swizzle operand
+  // from the 128-byte aligned address below the descriptor's start (a tile at
+  // 1056 was read from 1024)
+  unsigned char* tc_smem = tc_smem_raw + ((1024u - (saddr(tc_smem_raw) & 1023u)) & 1023u);
+
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&s_mma_done[0], 1);
+    mbar_init(&s_mma_done[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  constexpr uint32_t idesc = instr_desc(TM, TN);
+
+  bool failed = false;
+  for (int it = 0; it < nk; ++it) {
+    const int st = it & 1;
+    unsigned char* sA = tc_smem + st * STAGE_BYTES;
+    unsigned char* sB = sA + STAGE_BYTES / 2;
+    // the MMAs that read this buffer two iterations ago must be complete
+    if (it >= 2 && !failed && !mbar_wait(&s_mma_done[st], (uint32_t)((it - 2) >> 1) & 1u)) failed = true;
+    const int k0 = kb + it * TK;
+    // K beyond this split's chunk reads as zero
+    stage_operand<true>(g, sA, m0, k0, ke, tid);
+    stage_operand<false>(g, sB, n0, k0, ke, tid);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic stores -> tensor-core reads
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < TK / TKS; ++kk) {
+        const uint64_t ad = smem_desc(saddr(sA + kk * SUB_BYTES), 128, 256);
+        const uint64_t bd = smem_desc(saddr(sB + kk * SUB_BYTES), 128, 256);
+        tc_mma(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+      }
+      tc_commit(&s_mma_done[st]);
+    }
+  }
+  // all MMAs complete (they finish in issue order; the last commit covers them)
+  if (nk > 0 && !failed && !mbar_wait(&s_mma_done[(nk - 1) & 1], (uint32_t)((nk - 1) >> 1) & 1u)) failed = true;
+  if (failed) s_fail = 1;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  if (!s_fail) {
+    const int m = m0 + wid * 32 + lane;  // this thread's output row (TMEM lane)
+    const uint32_t trow = tmem + ((uint32_t)(wid * 32) << 16);
+    const double beta = g.beta_dev ? *g.beta_dev : g.beta;
+    const float alpha = (float)g.alpha;
+    const float rsm = (g.rs && m < g.M) ? (float)g.rs[m] : 1.f;
+    for (int c0 = 0; c0 < TN; c0 += 16) {
+      float v[16];
+      if (nk > 0) {
+        tc_ld16(trow + (uint32_t)c0, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      }
+      if (m >= g.M) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int n = n0 + c0 + i;
+        if (n >= g.N) break;
+        if (g.splits > 1) {
+          ((float*)g.partial)[(int64_t)blockIdx.z * g.M * g.N + (int64_t)m * g.N + n] = v[i];
+          continue;
+        }
+        float o = v[i] * alpha * rsm;
+        if (g.cs) o *= (float)g.cs[n];
+        const int64_t off = g.c_rowmaj ? (int64_t)m * g.ldc + n : (int64_t)m + (int64_t)n * g.ldc;
+        if (g.D != nullptr && beta != 0.0) {
+          const int64_t doff = g.c_rowmaj ? (int64_t)m * g.ldd + n : (int64_t)m + (int64_t)n * g.ldd;
+          float dv = ((const float*)g.D)[doff];
+          if (g.ds) dv *= (float)g.ds[n];
+          o += (float)beta * dv;
+        }
+        ((float*)g.C)[off] = o;
+      }
+    }
+  } else if (tid == 0) {
+    report(BKFAC_ETIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (wid == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+}  // namespace
+
+bool tc_gemm_enabled() { return true; }
+
+int tc_gemm_run(const GemmArgs& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return (int)cudaSuccess;
+  if (g.sym) return (int)cudaErrorInvalidValue;
+  GemmArgs a = g;
+  const int K = a.K0 + a.K1;
+  const int64_t tiles = ceil_div(a.M, TM) * ceil_div(a.N, TN);
+  // split K so that about two CTAs per SM are busy, within the partial buffer
+  int64_t splits = 1;
+  if (a.partial != nullptr && tiles < 2 * 152 && K > 4 * TK) {
+    const int64_t room = (int64_t)(a.partial_bytes / ((size_t)a.M * a.N * sizeof(float)));
+    splits = std::min<int64_t>(std::min<int64_t>(ceil_div(2 * 152, tiles), (int64_t)K / (2 * TK)), room);
+    splits = std::max<int64_t>(1, std::min<int64_t>(splits, 32));
+  }
+  a.k_chunk = (int)round_up(ceil_div(std::max(K, 1), splits), TK);
+  a.splits = (int)std::max<int64_t>(1, ceil_div(std::max(K, 1), a.k_chunk));
+  static std::atomic<int> configured{0};  // attribute set once (the call can stall the host)
+  if (!configured.load()) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * STAGE_BYTES + 1024);
+    if (e != cudaSuccess) return (int)e;
+    configured.store(1);
+  }
+  dim3 grid((unsigned)ceil_div(a.N, TN), (unsigned)ceil_div(a.M, TM), (unsigned)a.splits);
+  tc_gemm_kernel<<<grid, TC_THREADS, 2 * STAGE_BYTES + 1024, s>>>(a);
+  note_launches(1);
+  if (a.splits > 1) return splitk_reduce_f32(a, s);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace bkfac

@@ -116,6 +116,14 @@ def test_dense_path_wider(oracle):
     one_step_parity(oracle, 90, 64, 40, bkfac.F64, steps=2)
 
 
+@pytest.mark.parametrize("d,r,n", [(10, 10, 256), (10, 10, 255), (12, 12, 500)])
+def test_dense_path_wide_batch(oracle, d, r, n):
+    """A 10-wide output layer's Gamma with a whole minibatch of columns: the
+    eigensolve's column padding is at its largest (cluster of 16, block width
+    rounded up to the register-blocking width)."""
+    one_step_parity(oracle, d, r, n, bkfac.F32, steps=2)
+
+
 def test_init_keeps_rank_n_when_n_below_r(oracle):
     f, _ = one_step_parity(oracle, 200, 30, 8, bkfac.F64, steps=3)
     assert f.r_cur == 30
