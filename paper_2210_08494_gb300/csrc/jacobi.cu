@@ -550,23 +550,12 @@ __device__ __forceinline__ void bulk_push(uint32_t dst_cluster, const void* src,
       "r"(smem_addr(src)), "r"(bytes), "r"(mbar_cluster)
       : "memory");
 }
+// split cluster barrier: arrive (release) now, wait (acquire) later
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 // make this thread's generic-proxy shared-memory writes visible to the async proxy
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Block exchange between rounds.
-// DSM = true: the blocks stay in shared memory (two buffers) and move between
-// CTAs of the cluster.  Under the circle method the block at slot q >= 1 in
-// round t moves to slot q - 1 in round t + 1 (slot 1 wraps to slot 2C - 1;
-// slot 0 is fixed); slot s < C belongs to CTA s as its first block, slot s >= C
-// to CTA 2C - 1 - s as its second.  After a round every CTA pushes its two
-// blocks (and their stamps) with bulk asynchronous copies straight into the
-// other buffer of their next holders, where the copies complete on that
-// buffer's mbarrier; one cluster barrier before the pushes guarantees that
-// every destination buffer has been consumed.  DSM = false: blocks go back to
-// global memory (L2) between rounds (used when two buffers do not fit).
-//
-// Stamps: s_stamp[buffer][half * 32 + c] for column c of block `half` (b <= 32),
-// so that each block's stamps are one 128-byte transfer.
 // columns per warp and block in the register-blocked rounds (K) and the largest
 // block (K columns per warp, b <= 32): four FP32 columns of up to 512 rows per
 // warp (8 columns x 16 registers in flight); two for longer FP32 columns and
@@ -577,6 +566,24 @@ struct PairK {
   static constexpr int kMaxThreads = 32 * (32 / K);
 };
 
+// Block exchange between rounds.
+// DSM = true: the blocks stay in shared memory (three buffers) and move between
+// CTAs of the cluster.  Under the circle method the block at slot q >= 1 in
+// round t moves to slot q - 1 in round t + 1 (slot 1 wraps to slot 2C - 1;
+// slot 0 is fixed); slot s < C belongs to CTA s as its first block, slot s >= C
+// to CTA 2C - 1 - s as its second.  After a round every CTA pushes its two
+// blocks (and their stamps) with bulk asynchronous copies straight into the
+// next buffer of their next holders, where the copies complete on that
+// buffer's mbarrier.  The buffer written at the end of round t was last used
+// in round t - 2 and pushed out at its end; those pushes completed before any
+// CTA started round t - 1, so it is free once every CTA has finished round
+// t - 1.  That condition is a split cluster barrier: each CTA arrives after
+// computing a round and waits one round later, just before its pushes, by which
+// time the other CTAs have almost always arrived.  DSM = false: blocks go back
+// to global memory (L2) between rounds (used when three buffers do not fit).
+//
+// Stamps: s_stamp[buffer][half * 32 + c] for column c of block `half` (b <= 32),
+// so that each block's stamps are one 128-byte transfer.
 template <typename J, int NV, bool DSM>
 __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const __grid_constant__ JacobiBatch batch, double tol,
                                                       int max_sweeps) {
@@ -594,8 +601,8 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
   __shared__ int s_stop;
   __shared__ double s_tiny;
   __shared__ J s_nrm[64];                       // squared norms of the 2b staged columns
-  __shared__ __align__(16) int s_stamp[2][64];  // sweep of each staged column's last rotation (per buffer)
-  __shared__ __align__(8) uint64_t s_full[2];   // per buffer: the incoming blocks have landed
+  __shared__ __align__(16) int s_stamp[3][64];  // sweep of each staged column's last rotation (per buffer)
+  __shared__ __align__(8) uint64_t s_full[3];   // per buffer: the incoming blocks have landed
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nthr = blockDim.x;
@@ -603,7 +610,7 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
   J* W = (J*)P.W;
   int* stamp = P.stamp;
   J* buf0 = (J*)smem_raw;
-  J* buf1 = buf0 + (DSM ? (int64_t)2 * b * rp : 0);
+  auto buffer = [&](int k) { return buf0 + (DSM ? (int64_t)k * 2 * b * rp : 0); };
   const uint32_t blk_bytes = (uint32_t)((size_t)b * rp * sizeof(J));
   if (wid == 0) {
     // deterministic: fixed lane assignment, fixed shuffle tree
@@ -618,8 +625,9 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
   }
   const int nvec = b * rp / Vec<J>::W;  // vectors per block
   int cur = 0;
-  uint32_t phase[2] = {0u, 0u};
+  uint32_t phase[3] = {0u, 0u, 0u};
   bool aborted = false;
+  bool pending = false;  // this CTA has arrived on the cluster barrier and not yet waited
   if (DSM) {
     // initial blocks of round 0 from global memory
     const int bI = circle_pos(crank, 0, nblk), bJ = circle_pos(nblk - 1 - crank, 0, nblk);
@@ -630,6 +638,7 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
     if (tid == 0) {
       mbar_init(&s_full[0], 1);
       mbar_init(&s_full[1], 1);
+      mbar_init(&s_full[2], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     cluster.sync();  // every CTA's barriers are initialised before any push targets them
@@ -645,7 +654,7 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
     for (int t = 0; t < nblk - 1; ++t) {
       const int bI = circle_pos(crank, t, nblk);
       const int bJ = circle_pos(nblk - 1 - crank, t, nblk);
-      J* sm = (DSM && cur) ? buf1 : buf0;
+      J* sm = buffer(cur);
       int* st = s_stamp[DSM ? cur : 0];
       if (!DSM) {
         copy_vecs(reinterpret_cast<V*>(sm), reinterpret_cast<const V*>(W + (int64_t)bI * b * rp), nvec, tid, nthr);
@@ -672,12 +681,13 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
         // write-backs before any CTA of the cluster loads the blocks in the next round
         cluster.sync();
       } else {
-        const int nxt = cur ^ 1;
+        const int nxt = cur == 2 ? 0 : cur + 1;
         fence_proxy_async_smem();  // this round's rotations, visible to the bulk copies
-        cluster.sync();            // every CTA has finished this round: all destination buffers are free
+        if (pending) cluster_wait();  // every CTA has finished the previous round: buffer nxt is free everywhere
+        __syncthreads();
         if (tid == 0) {
           mbar_arrive_expect_tx(&s_full[nxt], 2u * (blk_bytes + 128u));
-          J* dst_buf = nxt ? buf1 : buf0;
+          J* dst_buf = buffer(nxt);
           for (int half = 0; half < 2; ++half) {
             const int slot = half == 0 ? crank : nblk - 1 - crank;
             const int to = slot == 0 ? 0 : (slot >= 2 ? slot - 1 : nblk - 1);
@@ -690,6 +700,8 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
                       mbar);
           }
         }
+        cluster_arrive();  // this round is computed (and its blocks are on their way)
+        pending = true;
         if (!aborted && !mbar_wait_bounded(&s_full[nxt], phase[nxt])) {
           aborted = true;
           s_abort[0] = 1;  // benign race: every writer stores 1
@@ -700,6 +712,10 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
       }
     }
     if (tid == 0) s_cnt[sweep & 1] = s_rot;
+    if (pending) {
+      cluster_wait();
+      pending = false;
+    }
     cluster.sync();
     if (tid == 0) {
       int total = 0, abort_any = 0;
@@ -727,7 +743,7 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
     // holds the blocks of the round after last_t
     const int tn = last_t + 1;
     const int bI = circle_pos(crank, tn, nblk), bJ = circle_pos(nblk - 1 - crank, tn, nblk);
-    const J* sm = cur ? buf1 : buf0;
+    const J* sm = buffer(cur);
     copy_vecs(reinterpret_cast<V*>(W + (int64_t)bI * b * rp), reinterpret_cast<const V*>(sm), nvec, tid, nthr);
     copy_vecs(reinterpret_cast<V*>(W + (int64_t)bJ * b * rp), reinterpret_cast<const V*>(sm + (int64_t)b * rp), nvec,
               tid, nthr);
@@ -860,13 +876,13 @@ int launch_jacobi_mode(const JacobiProblem* probs, int nprob, int C, DType j_t, 
     smem = std::max(smem, jacobi_smem_bytes(probs[i].b, probs[i].rows_pad, j_t));
   }
   if (b < 2 || b > 32 || (b & 1) || smem > 200 * 1024) return (int)cudaErrorInvalidValue;
-  // block exchange between rounds: over distributed shared memory (two buffers)
+  // block exchange between rounds: over distributed shared memory (three buffers)
   // when asked for and the buffers fit, else through L2
-  const bool dsm = want_dsm && 2 * smem <= 200 * 1024;
+  const bool dsm = want_dsm && 3 * smem <= 200 * 1024;
   if (j_t == DT_F64)
-    return dsm ? launch_nv<double, true>(batch, nprob, C, b, rp, 2 * smem, tol, max_sweeps, s)
+    return dsm ? launch_nv<double, true>(batch, nprob, C, b, rp, 3 * smem, tol, max_sweeps, s)
                : launch_nv<double, false>(batch, nprob, C, b, rp, smem, tol, max_sweeps, s);
-  return dsm ? launch_nv<float, true>(batch, nprob, C, b, rp, 2 * smem, tol, max_sweeps, s)
+  return dsm ? launch_nv<float, true>(batch, nprob, C, b, rp, 3 * smem, tol, max_sweeps, s)
              : launch_nv<float, false>(batch, nprob, C, b, rp, smem, tol, max_sweeps, s);
 }
 

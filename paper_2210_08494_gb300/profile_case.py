@@ -37,6 +37,17 @@ def factor_with_updates(d, r, n, dtype, updates, seed, alpha):
     return f
 
 
+def factor_with_state(d, r, dtype, seed):
+    """A factor holding r orthonormal columns and a power-law spectrum (no updates)."""
+    import numpy as np
+
+    f = bkfac.Factor(d, r, dtype)
+    Ut = synth.orthonormal_columns(d, r, seed)
+    sig = np.arange(1, r + 1, dtype=np.float64) ** -1.2
+    f.load_state(torch.from_numpy(Ut).to(f.torch_dtype).cuda(), torch.from_numpy(sig).cuda())
+    return f
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--d", type=int, default=4097)
@@ -46,16 +57,24 @@ def main(argv=None):
     ap.add_argument("--dtype", choices=sorted(DTYPES), default="f32")
     ap.add_argument("--alpha", type=float, default=1.2)
     ap.add_argument("--apply", type=int, default=0, metavar="D_OUT")
+    ap.add_argument("--synthetic-state", action="store_true",
+                    help="with --apply: load orthonormal factor states instead of running updates")
     args = ap.parse_args(argv)
     bkfac.load()
     bkfac.bkfac_status()
     dtype = DTYPES[args.dtype]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record()
-    fA = factor_with_updates(args.d, args.r, args.n, dtype, args.updates, 2000, args.alpha)
+    if args.synthetic_state:
+        fA = factor_with_state(args.d, args.r, dtype, 2000)
+    else:
+        fA = factor_with_updates(args.d, args.r, args.n, dtype, args.updates, 2000, args.alpha)
     end.record()
     if args.apply:
-        fG = factor_with_updates(args.apply, args.r, args.n, dtype, args.updates, 2001, args.alpha)
+        if args.synthetic_state:
+            fG = factor_with_state(args.apply, args.r, dtype, 2001)
+        else:
+            fG = factor_with_updates(args.apply, args.r, args.n, dtype, args.updates, 2001, args.alpha)
         tdt = torch.float64 if dtype == bkfac.F64 else torch.float32
         G = bkfac.grad_tensor(args.apply, args.d, tdt)
         G.normal_(generator=torch.Generator(device="cuda").manual_seed(7))
