@@ -14,8 +14,10 @@
 // the current one; one thread issues the MMAs and commits them to the buffer's
 // mbarrier, which releases the buffer for reuse.  The accumulator lives in 128
 // TMEM columns; the epilogue reads it back with tcgen05.ld (warp w reads TMEM
-// lanes 32w .. 32w + 31, i.e. output rows), applies the scaling and writes C,
-// or a split-K partial that splitk_reduce sums in a fixed order.
+// lanes 32w .. 32w + 31, i.e. output rows) into a shared-memory tile, from
+// which rows (row-major C, split-K partials) or columns (column-major C) leave
+// with coalesced accesses after the scaling; splitk_reduce sums partials in a
+// fixed order.
 //
 // Shared-memory operand layout: K-major, no swizzle.  Each K step of 16 is a
 // 128 x 16 sub-tile (4 KB) built from 8 x 16-byte "core matrices" (8 rows of 8
@@ -32,11 +34,26 @@
 namespace bkfac {
 namespace {
 
-constexpr int TM = 128, TN = 128, TK = 64, TKS = 16;  // tile M, N, staged K, K per MMA
+constexpr int TM = 128, TN = 128;  // output tile
 constexpr int TC_THREADS = 128;
-constexpr int SUB_BYTES = TM * TKS * 2;         // one 128 x 16 BF16 sub-tile
-constexpr int STAGE_BYTES = 2 * (TK / TKS) * SUB_BYTES;  // A and B, 4 sub-tiles each
+constexpr int SUB_BYTES = 4096;  // one 128-row operand sub-tile: the K of one MMA (32 bytes per row)
 constexpr int TMEM_COLS = 128;
+constexpr int TLD = TN + 1;  // leading dimension of the staged output tile (floats)
+
+// Operand encodings.  BF16 (X3 = false): one operand tile per matrix, K = 16 per
+// MMA.  3xTF32 (X3 = true): each FP32 value x is split into hi = tf32(x) and
+// lo = tf32(x - hi); D += A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped
+// A_lo B_lo term is below 2^-22 |a b|, FP32 accumulation), K = 8 per MMA.
+// Either way a stage holds four MMA sub-tiles of each operand tile.
+template <bool X3>
+struct TcMode {
+  static constexpr int EPC = X3 ? 4 : 8;       // elements per 16-byte core-matrix row
+  static constexpr int KPM = X3 ? 8 : 16;      // K per MMA
+  static constexpr int TK = 4 * KPM;           // K per stage
+  static constexpr int TILES = X3 ? 4 : 2;     // A(hi, lo), B(hi, lo) or A, B
+  static constexpr int STAGE_BYTES = TILES * 4 * SUB_BYTES;
+  static constexpr int SMEM_BYTES = (2 * STAGE_BYTES > TM * TLD * 4 ? 2 * STAGE_BYTES : TM * TLD * 4) + 1024;
+};
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -47,9 +64,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major
-__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+// instruction descriptor: FP32 accumulator, A and B both K-major, operand format
+// 1 = BF16 (kind::f16) or 2 = TF32 (kind::tf32)
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n, uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
@@ -75,13 +93,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+template <bool X3>
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                        uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
+  if constexpr (X3)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
@@ -131,10 +157,45 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// byte offset of element (row, k) (k in [0, 64)) of a staged 128 x 64 operand:
-// sub-tile k / 16, then core matrix (row / 8, (k mod 16) / 8), then row mod 8
+// byte offset of the 16-byte core-matrix row holding elements (row, k .. k + EPC
+// - 1) of a staged operand tile (k a multiple of EPC): MMA sub-tile k / KPM,
+// then core matrix (row / 8, (k mod KPM) / EPC), then row mod 8
+template <bool X3>
 __device__ __forceinline__ uint32_t tile_off(int row, int k) {
-  return (uint32_t)((k >> 4) * SUB_BYTES + (row >> 3) * 256 + ((k >> 3) & 1) * 128 + (row & 7) * 16);
+  using Md = TcMode<X3>;
+  return (uint32_t)((k / Md::KPM) * SUB_BYTES + (row >> 3) * 256 + ((k % Md::KPM) / Md::EPC) * 128 + (row & 7) * 16);
+}
+
+// TF32 rounding (to nearest, ties away) of an FP32 value, as FP32 bits
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// store one 16-byte group of EPC consecutive-K elements: BF16 into tile 0, or
+// the TF32 hi / lo parts into tiles 0 / 1
+template <bool X3>
+__device__ __forceinline__ void put_group(unsigned char* t0, unsigned char* t1, uint32_t off, const float* v) {
+  if constexpr (X3) {
+    uint4 hi, lo;
+    uint32_t* h = reinterpret_cast<uint32_t*>(&hi);
+    uint32_t* l = reinterpret_cast<uint32_t*>(&lo);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      h[e] = to_tf32(v[e]);
+      l[e] = to_tf32(v[e] - __uint_as_float(h[e]));
+    }
+    *reinterpret_cast<uint4*>(t0 + off) = hi;
+    *reinterpret_cast<uint4*>(t1 + off) = lo;
+  } else {
+    uint4 q;
+    q.x = pack_bf16(v[0], v[1]);
+    q.y = pack_bf16(v[2], v[3]);
+    q.z = pack_bf16(v[4], v[5]);
+    q.w = pack_bf16(v[6], v[7]);
+    *reinterpret_cast<uint4*>(t0 + off) = q;
+  }
 }
 
 // Segment of the concatenated operand holding K index k (k < K), the element
@@ -159,49 +220,48 @@ __device__ __forceinline__ Seg seg_of(const GemmArgs& g, int k) {
   return s;
 }
 
-// Stage rows [r0, r0 + 128) x K block [k0, k0 + 64) of one operand into `dst`
-// (BF16, canonical layout); rows >= R (M or N) and K >= K read as zero.
-// `kmaj`: the operand's K index is contiguous in memory.  Work items are 8
-// consecutive K of one row (one 16-byte core-matrix row): K-contiguous operands
-// are read along K (8 lanes per 256-byte row segment, two 16-byte loads per
-// item), the others along rows (lanes over 4-row groups, one 16-byte load per
-// K).  Items that straddle an edge, the K0 seam or a misaligned start fall back
-// to element loads.
-template <bool IS_A>
-__device__ __forceinline__ void stage_operand(const GemmArgs& g, unsigned char* dst, int r0, int k0, int K, int tid) {
+// Stage rows [r0, r0 + 128) x K block [k0, k0 + TK) of one operand into its
+// tile(s) t0 (and t1 for the TF32 lo parts), canonical layout; rows >= R (M or
+// N) and K >= K read as zero.  `kmaj`: the operand's K index is contiguous in
+// memory.  Work items are EPC consecutive K of one row (one 16-byte core-matrix
+// row): K-contiguous operands are read along K (16-byte loads, 8 lanes per row
+// segment), the others along rows (lanes over 4-row groups, one 16-byte load
+// per K).  Items that straddle an edge, the K0 seam or a misaligned start fall
+// back to element loads.
+template <bool X3, bool IS_A>
+__device__ __forceinline__ void stage_operand(const GemmArgs& g, unsigned char* t0, unsigned char* t1, int r0, int k0,
+                                              int K, int tid) {
+  constexpr int EPC = TcMode<X3>::EPC, CH = TcMode<X3>::TK / EPC;  // 8 chunks per row either way
   const bool kmaj = IS_A ? g.a_kmaj : g.b_kmaj;
   const int R = IS_A ? g.M : g.N;
   if (kmaj) {
-    for (int it = tid; it < TM * 8; it += TC_THREADS) {
-      const int row = it >> 3, kc = (it & 7) * 8;
+    for (int it = tid; it < TM * CH; it += TC_THREADS) {
+      const int row = it / CH, kc = (it % CH) * EPC;
       const int gr = r0 + row, gk = k0 + kc;
-      float v[8];
+      float v[EPC];
       const Seg sg = seg_of<IS_A>(g, min(gk, max(K - 1, 0)));
-      const bool fast = gr < R && gk + 8 <= K && (gk >= g.K0 || gk + 8 <= g.K0) && sg.vec && (sg.k & 3) == 0;
+      const bool fast = gr < R && gk + EPC <= K && (gk >= g.K0 || gk + EPC <= g.K0) && sg.vec && (sg.k & 3) == 0;
       if (fast) {
         const float4* q = reinterpret_cast<const float4*>(sg.p + (int64_t)gr * sg.ld + sg.k);
-        const float4 x0 = __ldg(q), x1 = __ldg(q + 1);
-        v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
-        v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+#pragma unroll
+        for (int h = 0; h < EPC / 4; ++h) {
+          const float4 x = __ldg(q + h);
+          v[4 * h] = x.x; v[4 * h + 1] = x.y; v[4 * h + 2] = x.z; v[4 * h + 3] = x.w;
+        }
       } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = IS_A ? ld_a(g, gr, gk + e, K) : ld_b(g, gr, gk + e, K);
+        for (int e = 0; e < EPC; ++e) v[e] = IS_A ? ld_a(g, gr, gk + e, K) : ld_b(g, gr, gk + e, K);
       }
-      uint4 q;
-      q.x = pack_bf16(v[0], v[1]);
-      q.y = pack_bf16(v[2], v[3]);
-      q.z = pack_bf16(v[4], v[5]);
-      q.w = pack_bf16(v[6], v[7]);
-      *reinterpret_cast<uint4*>(dst + tile_off(row, kc)) = q;
+      put_group<X3>(t0, t1, tile_off<X3>(row, kc), v);
     }
   } else {
-    for (int it = tid; it < (TM / 4) * 8; it += TC_THREADS) {
-      const int rq = (it & 31) * 4, kc = (it >> 5) * 8;
+    for (int it = tid; it < (TM / 4) * CH; it += TC_THREADS) {
+      const int rq = (it & 31) * 4, kc = (it >> 5) * EPC;
       const int gr = r0 + rq, gk = k0 + kc;
-      float v[4][8];
+      float v[4][EPC];
       const bool rows_in = gr + 4 <= R;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
+      for (int e = 0; e < EPC; ++e) {
         const int k = gk + e;
         bool done = false;
         if (rows_in && k < K) {
@@ -217,19 +277,15 @@ __device__ __forceinline__ void stage_operand(const GemmArgs& g, unsigned char* 
           for (int i = 0; i < 4; ++i) v[i][e] = IS_A ? ld_a(g, gr + i, k, K) : ld_b(g, gr + i, k, K);
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        uint4 q;
-        q.x = pack_bf16(v[i][0], v[i][1]);
-        q.y = pack_bf16(v[i][2], v[i][3]);
-        q.z = pack_bf16(v[i][4], v[i][5]);
-        q.w = pack_bf16(v[i][6], v[i][7]);
-        *reinterpret_cast<uint4*>(dst + tile_off(rq + i, kc)) = q;
-      }
+      for (int i = 0; i < 4; ++i) put_group<X3>(t0, t1, tile_off<X3>(rq + i, kc), v[i]);
     }
   }
 }
 
+template <bool X3>
 __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const GemmArgs g) {
+  using Md = TcMode<X3>;
+  constexpr int TK = Md::TK, STAGE_BYTES = Md::STAGE_BYTES;
   extern __shared__ __align__(16) unsigned char tc_smem_raw[];  // only 16 bytes are guaranteed
   __shared__ __align__(8) uint64_t s_mma_done[2];
   __shared__ uint32_t s_tmem;
@@ -263,29 +319,37 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const GemmArgs g) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  constexpr uint32_t idesc = instr_desc(TM, TN);
+  constexpr uint32_t idesc = instr_desc(TM, TN, X3 ? 2u : 1u);
 
   bool failed = false;
   for (int it = 0; it < nk; ++it) {
     const int st = it & 1;
-    unsigned char* sA = tc_smem + st * STAGE_BYTES;
-    unsigned char* sB = sA + STAGE_BYTES / 2;
+    unsigned char* sA = tc_smem + st * STAGE_BYTES;              // A (hi)
+    unsigned char* sB = sA + STAGE_BYTES / Md::TILES * (X3 ? 2 : 1);  // B (hi)
+    unsigned char* sAl = sA + 4 * SUB_BYTES;                       // A lo (TF32 only)
+    unsigned char* sBl = sB + 4 * SUB_BYTES;                       // B lo (TF32 only)
     // the MMAs that read this buffer two iterations ago must be complete
     if (it >= 2 && !failed && !mbar_wait(&s_mma_done[st], (uint32_t)((it - 2) >> 1) & 1u)) failed = true;
     const int k0 = kb + it * TK;
     // K beyond this split's chunk reads as zero
-    stage_operand<true>(g, sA, m0, k0, ke, tid);
-    stage_operand<false>(g, sB, n0, k0, ke, tid);
+    stage_operand<X3, true>(g, sA, sAl, m0, k0, ke, tid);
+    stage_operand<X3, false>(g, sB, sBl, n0, k0, ke, tid);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic stores -> tensor-core reads
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
 #pragma unroll
-      for (int kk = 0; kk < TK / TKS; ++kk) {
+      for (int kk = 0; kk < 4; ++kk) {
         const uint64_t ad = smem_desc(saddr(sA + kk * SUB_BYTES), 128, 256);
         const uint64_t bd = smem_desc(saddr(sB + kk * SUB_BYTES), 128, 256);
-        tc_mma(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+        tc_mma<X3>(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+        if constexpr (X3) {
+          const uint64_t adl = smem_desc(saddr(sAl + kk * SUB_BYTES), 128, 256);
+          const uint64_t bdl = smem_desc(saddr(sBl + kk * SUB_BYTES), 128, 256);
+          tc_mma<X3>(tmem, ad, bdl, idesc, 1u);
+          tc_mma<X3>(tmem, adl, bd, idesc, 1u);
+        }
       }
       tc_commit(&s_mma_done[st]);
     }
@@ -298,38 +362,92 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const GemmArgs g) {
   tc_fence_after();
 
   if (!s_fail) {
-    const int m = m0 + wid * 32 + lane;  // this thread's output row (TMEM lane)
-    const uint32_t trow = tmem + ((uint32_t)(wid * 32) << 16);
-    const double beta = g.beta_dev ? *g.beta_dev : g.beta;
-    const float alpha = (float)g.alpha;
-    const float rsm = (g.rs && m < g.M) ? (float)g.rs[m] : 1.f;
-    for (int c0 = 0; c0 < TN; c0 += 16) {
-      float v[16];
-      if (nk > 0) {
-        tc_ld16(trow + (uint32_t)c0, v);
-      } else {
+    // accumulator -> shared tile T (row-major, ld 129: conflict-free whether lanes
+    // run over rows or over columns); the operand buffers are free now
+    float* T = reinterpret_cast<float*>(tc_smem);
+    {
+      const int row = wid * 32 + lane;
+      const uint32_t trow = tmem + ((uint32_t)(wid * 32) << 16);
+      for (int c0 = 0; c0 < TN; c0 += 16) {
+        float v[16];
+        if (nk > 0) {
+          tc_ld16(trow + (uint32_t)c0, v);
+        } else {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) T[row * TLD + c0 + i] = v[i];
       }
-      if (m >= g.M) continue;
+    }
+    __syncthreads();
+    const float beta = (float)(g.beta_dev ? *g.beta_dev : g.beta);
+    const float alpha = (float)g.alpha;
+    const bool with_d = g.D != nullptr && beta != 0.f && g.splits == 1;
+    if (g.c_rowmaj || g.splits > 1) {
+      // rows go out whole: lane l owns columns 4l .. 4l + 3 of the tile
+      const int n = n0 + 4 * lane;
+      float csv[4], dsv[4];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int n = n0 + c0 + i;
-        if (n >= g.N) break;
-        if (g.splits > 1) {
-          ((float*)g.partial)[(int64_t)blockIdx.z * g.M * g.N + (int64_t)m * g.N + n] = v[i];
-          continue;
+      for (int j = 0; j < 4; ++j) {
+        const bool in = n + j < g.N;
+        csv[j] = (g.cs && in) ? (float)g.cs[n + j] : 1.f;
+        dsv[j] = (g.ds && in) ? (float)g.ds[n + j] : 1.f;
+      }
+      float* out = g.splits > 1 ? (float*)g.partial + (int64_t)blockIdx.z * g.M * g.N : (float*)g.C;
+      const int64_t ldo = g.splits > 1 ? g.N : g.ldc;
+      const bool vec_o = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) && (ldo & 3) == 0;
+      const bool vec_d = with_d && ((reinterpret_cast<uintptr_t>(g.D) & 15u) == 0) && (g.ldd & 3) == 0;
+      for (int r = wid; r < TM; r += TC_THREADS / 32) {
+        const int m = m0 + r;
+        if (m >= g.M || n >= g.N) continue;
+        const float rsm = (g.splits == 1 && g.rs) ? (float)g.rs[m] : 1.f;
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          o[j] = T[r * TLD + 4 * lane + j];
+          if (g.splits == 1) o[j] *= alpha * rsm * csv[j];
         }
-        float o = v[i] * alpha * rsm;
-        if (g.cs) o *= (float)g.cs[n];
-        const int64_t off = g.c_rowmaj ? (int64_t)m * g.ldc + n : (int64_t)m + (int64_t)n * g.ldc;
-        if (g.D != nullptr && beta != 0.0) {
-          const int64_t doff = g.c_rowmaj ? (int64_t)m * g.ldd + n : (int64_t)m + (int64_t)n * g.ldd;
-          float dv = ((const float*)g.D)[doff];
-          if (g.ds) dv *= (float)g.ds[n];
-          o += (float)beta * dv;
+        const bool full = n + 4 <= g.N;
+        if (with_d) {
+          const float* drow = (const float*)g.D + (int64_t)m * g.ldd + n;
+          float dv[4];
+          if (full && vec_d) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(drow));
+            dv[0] = q.x; dv[1] = q.y; dv[2] = q.z; dv[3] = q.w;
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) dv[j] = n + j < g.N ? drow[j] : 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) o[j] += beta * dv[j] * dsv[j];
         }
-        ((float*)g.C)[off] = o;
+        float* orow = out + (int64_t)m * ldo + n;
+        if (full && vec_o) {
+          *reinterpret_cast<float4*>(orow) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (n + j < g.N) orow[j] = o[j];
+        }
+      }
+    } else {
+      // column-major C: lanes run over 32 consecutive rows of one column
+      for (int rb = 0; rb < TM; rb += 32) {
+        const int r = rb + lane, m = m0 + r;
+        const float rsm = (g.rs && m < g.M) ? (float)g.rs[m] : 1.f;
+        for (int c = wid; c < TN; c += TC_THREADS / 32) {
+          const int n = n0 + c;
+          if (m >= g.M || n >= g.N) continue;
+          float o = T[r * TLD + c] * alpha * rsm;
+          if (g.cs) o *= (float)g.cs[n];
+          if (with_d) {
+            float dv = ((const float*)g.D)[m + (int64_t)n * g.ldd];
+            if (g.ds) dv *= (float)g.ds[n];
+            o += beta * dv;
+          }
+          ((float*)g.C)[m + (int64_t)n * g.ldc] = o;
+        }
       }
     }
   } else if (tid == 0) {
@@ -345,35 +463,46 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const GemmArgs g) {
 
 }  // namespace
 
-bool tc_gemm_enabled() { return true; }
+namespace {
 
-int tc_gemm_run(const GemmArgs& g, cudaStream_t s) {
-  if (g.M <= 0 || g.N <= 0) return (int)cudaSuccess;
-  if (g.sym) return (int)cudaErrorInvalidValue;
+template <bool X3>
+int tc_launch(const GemmArgs& g, cudaStream_t s) {
+  using Md = TcMode<X3>;
   GemmArgs a = g;
   const int K = a.K0 + a.K1;
   const int64_t tiles = ceil_div(a.M, TM) * ceil_div(a.N, TN);
   // split K so that about two CTAs per SM are busy, within the partial buffer
   int64_t splits = 1;
-  if (a.partial != nullptr && tiles < 2 * 152 && K > 4 * TK) {
+  if (a.partial != nullptr && tiles < 2 * 152 && K > 4 * Md::TK) {
     const int64_t room = (int64_t)(a.partial_bytes / ((size_t)a.M * a.N * sizeof(float)));
-    splits = std::min<int64_t>(std::min<int64_t>(ceil_div(2 * 152, tiles), (int64_t)K / (2 * TK)), room);
+    splits = std::min<int64_t>(std::min<int64_t>(ceil_div(2 * 152, tiles), (int64_t)K / (2 * Md::TK)), room);
     splits = std::max<int64_t>(1, std::min<int64_t>(splits, 32));
   }
-  a.k_chunk = (int)round_up(ceil_div(std::max(K, 1), splits), TK);
+  a.k_chunk = (int)round_up(ceil_div(std::max(K, 1), splits), Md::TK);
   a.splits = (int)std::max<int64_t>(1, ceil_div(std::max(K, 1), a.k_chunk));
   static std::atomic<int> configured{0};  // attribute set once (the call can stall the host)
   if (!configured.load()) {
     const cudaError_t e =
-        cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * STAGE_BYTES + 1024);
+        cudaFuncSetAttribute(tc_gemm_kernel<X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Md::SMEM_BYTES);
     if (e != cudaSuccess) return (int)e;
     configured.store(1);
   }
   dim3 grid((unsigned)ceil_div(a.N, TN), (unsigned)ceil_div(a.M, TM), (unsigned)a.splits);
-  tc_gemm_kernel<<<grid, TC_THREADS, 2 * STAGE_BYTES + 1024, s>>>(a);
+  tc_gemm_kernel<X3><<<grid, TC_THREADS, Md::SMEM_BYTES, s>>>(a);
   note_launches(1);
   if (a.splits > 1) return splitk_reduce_f32(a, s);
   return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_gemm_enabled() { return true; }
+
+// BF16 operands when the arguments ask for BF16 rounding, else 3xTF32
+int tc_gemm_run(const GemmArgs& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return (int)cudaSuccess;
+  if (g.sym) return (int)cudaErrorInvalidValue;
+  return g.round_bf16 ? tc_launch<false>(g, s) : tc_launch<true>(g, s);
 }
 
 }  // namespace bkfac
