@@ -545,6 +545,37 @@ def run_gpu(args, world, rank, local):
                "h2d_bytes_per_step": int((hXA.numel() + hXG.numel() + hG.numel()) * 4),
                "d2h_bytes_per_step": int(hS.numel() * 4), "ms_per_step": ms_e2e}
 
+    # ---- the same plain per-factor step with the FP32 products as 3xTF32 on the tensor cores
+    def plain_variant(flags):
+        gA = bkfac.Factor(D_A, R, bkfac.F32, device=dev, flags=flags)
+        gG = bkfac.Factor(D_G, R, bkfac.F32, device=dev, flags=flags)
+        bkfac.bkfac_init(gA, XA[0])
+        bkfac.bkfac_init(gG, XG[0])
+
+        def vstep(t):
+            bkfac.bkfac_update(gA, XA[1 + t % (POOL_X - 1)], RHO)
+            bkfac.bkfac_update(gG, XG[1 + t % (POOL_X - 1)], RHO)
+            bkfac.bkfac_apply(gA, gG, LAM, LAM, Gs[t % POOL_G], S)
+
+        for t in range(args.warmup):
+            vstep(t)
+        ve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for t in range(args.steps):
+            flush.zero_()
+            ve[t][0].record(stream)
+            vstep(args.warmup + t)
+            ve[t][1].record(stream)
+        torch.cuda.synchronize()
+        if bkfac.bkfac_status() != bkfac.OK:
+            raise RuntimeError("3xTF32 variant: device status not OK")
+        ms = shard.max_over_ranks(float(sum(a.elapsed_time(b) for a, b in ve)), device=dev) / args.steps
+        return {"value": 2.0 * 1000.0 / ms * world, "unit": "factor-updates/s", "ms_per_step": ms,
+                "path": "plain per-factor calls, FP32 products as 3xTF32 on the tensor cores (BKFAC_FLAG_TF32X3)",
+                "parity_bound": 1e-4}
+
+    variants = {} if args.no_batched else {"plain_f32_tf32x3": plain_variant(bkfac.FLAG_TF32X3)}
+
     batched = {} if args.no_batched else {
         "f32_graph": run_batched(args, bkfac, synth, torch, dev, seedA, seedG, bkfac.F32, flush),
         "mixed_bf16_graph": run_batched(args, bkfac, synth, torch, dev, seedA, seedG, bkfac.MIXED_BF16, flush),
@@ -570,6 +601,7 @@ def run_gpu(args, world, rank, local):
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in trace.items() if v[1]},
             "jacobi_sweeps": sweeps,
             "batched": batched,
+            "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -78,6 +78,11 @@ enum {
 
 /* ---- factor flags ------------------------------------------------------- */
 #define BKFAC_FLAG_EIG_FP64 (1u << 0) /* core eigensolve in FP64 also in F32 / MIXED modes */
+#define BKFAC_FLAG_TF32X3 (1u << 1)   /* F32 mode: the tall-skinny products (U^T X, U M, [U Q] V and
+                                         the inverse application's passes) on the tensor cores as
+                                         3xTF32 (hi/lo split, FP32 accumulation; relative error of a
+                                         product ~1e-5 at K = 4096 instead of ~1e-7); the apply takes
+                                         it when either factor carries it */
 
 /* ---- apply flags -------------------------------------------------------- */
 #define BKFAC_SPECTRUM_CONTINUATION (1u << 0) /* Sec. 3.5.1: lam += min sigma, sigma -= min sigma */

@@ -24,6 +24,7 @@ from . import build as _build
 F64, F32, MIXED_BF16 = 0, 1, 2
 OK, EINVAL, ENOTAPPLICABLE, ECHOL, ENOCONV, ENONFINITE, ETIMEOUT, ECUDA, EWORKSPACE, ENOMEM = range(10)
 FLAG_EIG_FP64 = 1
+FLAG_TF32X3 = 2
 SPECTRUM_CONTINUATION = 1
 OP_UPDATE, OP_REORTH = 0, 1
 

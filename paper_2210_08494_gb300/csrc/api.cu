@@ -51,6 +51,7 @@ bool dense_path(const bkfac_factor* f, int n) { return (int64_t)f->r + n >= f->d
 struct Prec {
   DType t, jt, acc;
   bool bf16;
+  bool x3;     // FP32 products as 3xTF32 on the tensor cores (BKFAC_FLAG_TF32X3)
   double u_t;  // unit roundoff governing the residual threshold
 };
 Prec prec_of(const bkfac_factor* f) {
@@ -58,6 +59,7 @@ Prec prec_of(const bkfac_factor* f) {
   p.t = dt_of(f->dtype);
   p.acc = p.t;
   p.bf16 = f->dtype == BKFAC_MIXED_BF16;
+  p.x3 = f->dtype == BKFAC_F32 && (f->flags & BKFAC_FLAG_TF32X3) != 0;
   p.jt = (f->dtype == BKFAC_F64 || (f->flags & BKFAC_FLAG_EIG_FP64)) ? DT_F64 : DT_F32;
   p.u_t = f->dtype == BKFAC_F64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
   return p;
@@ -208,6 +210,7 @@ struct ApplyPlan {
 ApplyPlan plan_apply(const bkfac_factor* fA, const bkfac_factor* fG, int kA, int kG) {
   ApplyPlan p{};
   p.pr = prec_of(fA);
+  p.pr.x3 = p.pr.x3 || prec_of(fG).x3;
   p.dA = fA->d;
   p.dG = fG->d;
   p.kA = kA;
@@ -403,6 +406,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     g.ldb0 = ldx;
     g.b_kmaj = true;
     g.round_bf16 = pr.bf16;
+    g.tf32x3 = pr.x3;
     g.C = M;
     g.ldc = p.ldm;
     g.splits = gemm_pick_splits(k, n, d, 152);
@@ -420,6 +424,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     h.ldb0 = p.ldm;
     h.b_kmaj = true;
     h.round_bf16 = pr.bf16;
+    h.tf32x3 = pr.x3;
     h.C = P;
     h.ldc = p.ldq;
     h.D = X;
@@ -505,6 +510,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   g.ldb1 = p.ldv;
   g.b_kmaj = true;
   g.round_bf16 = pr.bf16;
+  g.tf32x3 = pr.x3;
   g.C = at<void>(ws, p.o_Un);
   g.ldc = p.ldq;
   g.partial = part;
@@ -728,6 +734,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.ldb0 = fA->ldu;
     g.b_kmaj = true;
     g.round_bf16 = pr.bf16;
+    g.tf32x3 = pr.x3;
     g.C = T1;
     g.ldc = cap.ld1;
     g.partial = at<void>(ws, cap.o_part1);
@@ -746,6 +753,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.ldb0 = fG->ldu;
     g.b_kmaj = true;
     g.round_bf16 = pr.bf16;
+    g.tf32x3 = pr.x3;
     g.C = T2;  // column-major d_in x kG == row-major kG x d_in
     g.ldc = cap.ld2;
     g.cs = cGo;
@@ -810,6 +818,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.ldb1 = cap.ld2;
     g.b_kmaj = false;
     g.round_bf16 = pr.bf16;
+    g.tf32x3 = pr.x3;
     g.C = S;
     g.ldc = lds;
     g.c_rowmaj = true;

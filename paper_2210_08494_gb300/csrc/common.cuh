@@ -66,6 +66,7 @@ struct GemmArgs {
   const void* B1;
   int64_t ldb1;
   bool a_kmaj, b_kmaj, c_rowmaj, round_bf16;
+  bool tf32x3;     // FP32 operands: products as 3xTF32 on the tensor cores
   bool sym;        // C = A^T A with M == N and B == A: only upper tiles are computed
   void* C;
   int64_t ldc;

@@ -557,7 +557,8 @@ int splitk_reduce_f32(const GemmArgs& g, cudaStream_t s) {
 int gemm_run(const GemmArgs& g, DType in_t, DType acc_t, DType out_t, cudaStream_t s) {
   if (in_t == DT_F64 && acc_t == DT_F64 && out_t == DT_F64) return run_typed<double, double, double>(g, s);
   // mixed precision (BF16 operands, FP32 accumulation): the tensor cores
-  if (in_t == DT_F32 && acc_t == DT_F32 && out_t == DT_F32 && g.round_bf16 && !g.sym && tc_gemm_enabled())
+  if (in_t == DT_F32 && acc_t == DT_F32 && out_t == DT_F32 && (g.round_bf16 || g.tf32x3) && !g.sym &&
+      tc_gemm_enabled())
     return tc_gemm_run(g, s);
   if (in_t == DT_F32 && acc_t == DT_F32 && out_t == DT_F32) {
     if (large_ok(g)) {

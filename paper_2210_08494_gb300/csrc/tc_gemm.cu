@@ -220,45 +220,59 @@ __device__ __forceinline__ Seg seg_of(const GemmArgs& g, int k) {
   return s;
 }
 
-// Stage rows [r0, r0 + 128) x K block [k0, k0 + TK) of one operand into its
-// tile(s) t0 (and t1 for the TF32 lo parts), canonical layout; rows >= R (M or
-// N) and K >= K read as zero.  `kmaj`: the operand's K index is contiguous in
-// memory.  Work items are EPC consecutive K of one row (one 16-byte core-matrix
-// row): K-contiguous operands are read along K (16-byte loads, 8 lanes per row
-// segment), the others along rows (lanes over 4-row groups, one 16-byte load
-// per K).  Items that straddle an edge, the K0 seam or a misaligned start fall
-// back to element loads.
+// Staging of rows [r0, r0 + 128) x K block [k0, k0 + TK) of one operand into
+// its tile(s) t0 (and t1 for the TF32 lo parts), canonical layout; rows >= R
+// (M or N) and K >= K read as zero.  `kmaj`: the operand's K index is
+// contiguous in memory.  Work items are EPC consecutive K of one row (one
+// 16-byte core-matrix row): K-contiguous operands are read along K (16-byte
+// loads, 8 lanes per row segment), the others along rows (lanes over 4-row
+// groups, one 16-byte load per K).  Split in two so that the kernel can issue
+// the next stage's loads (up to sixteen 16-byte loads per thread in flight)
+// before it waits for the tensor core to release the buffer.  Items that
+// straddle an edge, the K0 seam or a misaligned start fall back to element
+// loads.
+template <bool X3>
+struct Stage {
+  static constexpr int EPC = TcMode<X3>::EPC, CH = TcMode<X3>::TK / EPC;  // 8 chunks per row either way
+  static constexpr int NK = TM * CH / TC_THREADS;                          // K-contiguous items per thread (8)
+  static constexpr int NR = (TM / 4) * CH / TC_THREADS;                    // row-contiguous items per thread (2)
+  static constexpr int VN = NK * EPC;                                      // == NR * 4 * EPC
+};
+
 template <bool X3, bool IS_A>
-__device__ __forceinline__ void stage_operand(const GemmArgs& g, unsigned char* t0, unsigned char* t1, int r0, int k0,
-                                              int K, int tid) {
-  constexpr int EPC = TcMode<X3>::EPC, CH = TcMode<X3>::TK / EPC;  // 8 chunks per row either way
+__device__ __forceinline__ void load_operand(const GemmArgs& g, int r0, int k0, int K, int tid,
+                                             float (&v)[Stage<X3>::VN]) {
+  using S = Stage<X3>;
+  constexpr int EPC = S::EPC, CH = S::CH;
   const bool kmaj = IS_A ? g.a_kmaj : g.b_kmaj;
   const int R = IS_A ? g.M : g.N;
   if (kmaj) {
-    for (int it = tid; it < TM * CH; it += TC_THREADS) {
+#pragma unroll
+    for (int q = 0; q < S::NK; ++q) {
+      const int it = tid + q * TC_THREADS;
       const int row = it / CH, kc = (it % CH) * EPC;
       const int gr = r0 + row, gk = k0 + kc;
-      float v[EPC];
       const Seg sg = seg_of<IS_A>(g, min(gk, max(K - 1, 0)));
       const bool fast = gr < R && gk + EPC <= K && (gk >= g.K0 || gk + EPC <= g.K0) && sg.vec && (sg.k & 3) == 0;
       if (fast) {
-        const float4* q = reinterpret_cast<const float4*>(sg.p + (int64_t)gr * sg.ld + sg.k);
+        const float4* src = reinterpret_cast<const float4*>(sg.p + (int64_t)gr * sg.ld + sg.k);
 #pragma unroll
         for (int h = 0; h < EPC / 4; ++h) {
-          const float4 x = __ldg(q + h);
-          v[4 * h] = x.x; v[4 * h + 1] = x.y; v[4 * h + 2] = x.z; v[4 * h + 3] = x.w;
+          const float4 x = __ldg(src + h);
+          v[q * EPC + 4 * h] = x.x; v[q * EPC + 4 * h + 1] = x.y;
+          v[q * EPC + 4 * h + 2] = x.z; v[q * EPC + 4 * h + 3] = x.w;
         }
       } else {
 #pragma unroll
-        for (int e = 0; e < EPC; ++e) v[e] = IS_A ? ld_a(g, gr, gk + e, K) : ld_b(g, gr, gk + e, K);
+        for (int e = 0; e < EPC; ++e) v[q * EPC + e] = IS_A ? ld_a(g, gr, gk + e, K) : ld_b(g, gr, gk + e, K);
       }
-      put_group<X3>(t0, t1, tile_off<X3>(row, kc), v);
     }
   } else {
-    for (int it = tid; it < (TM / 4) * CH; it += TC_THREADS) {
+#pragma unroll
+    for (int q = 0; q < S::NR; ++q) {
+      const int it = tid + q * TC_THREADS;
       const int rq = (it & 31) * 4, kc = (it >> 5) * EPC;
       const int gr = r0 + rq, gk = k0 + kc;
-      float v[4][EPC];
       const bool rows_in = gr + 4 <= R;
 #pragma unroll
       for (int e = 0; e < EPC; ++e) {
@@ -268,16 +282,39 @@ __device__ __forceinline__ void stage_operand(const GemmArgs& g, unsigned char* 
           const Seg sg = seg_of<IS_A>(g, k);
           if (sg.vec) {  // r0 and rq are multiples of 4: the 4 rows form one aligned vector
             const float4 x = __ldg(reinterpret_cast<const float4*>(sg.p + gr + (int64_t)sg.k * sg.ld));
-            v[0][e] = x.x; v[1][e] = x.y; v[2][e] = x.z; v[3][e] = x.w;
+            v[(q * 4 + 0) * EPC + e] = x.x; v[(q * 4 + 1) * EPC + e] = x.y;
+            v[(q * 4 + 2) * EPC + e] = x.z; v[(q * 4 + 3) * EPC + e] = x.w;
             done = true;
           }
         }
         if (!done)
 #pragma unroll
-          for (int i = 0; i < 4; ++i) v[i][e] = IS_A ? ld_a(g, gr + i, k, K) : ld_b(g, gr + i, k, K);
+          for (int i = 0; i < 4; ++i)
+            v[(q * 4 + i) * EPC + e] = IS_A ? ld_a(g, gr + i, k, K) : ld_b(g, gr + i, k, K);
       }
+    }
+  }
+}
+
+template <bool X3, bool IS_A>
+__device__ __forceinline__ void store_operand(const GemmArgs& g, unsigned char* t0, unsigned char* t1, int tid,
+                                              const float (&v)[Stage<X3>::VN]) {
+  using S = Stage<X3>;
+  constexpr int EPC = S::EPC, CH = S::CH;
+  const bool kmaj = IS_A ? g.a_kmaj : g.b_kmaj;
+  if (kmaj) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) put_group<X3>(t0, t1, tile_off<X3>(rq + i, kc), v[i]);
+    for (int q = 0; q < S::NK; ++q) {
+      const int it = tid + q * TC_THREADS;
+      put_group<X3>(t0, t1, tile_off<X3>(it / CH, (it % CH) * EPC), v + q * EPC);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < S::NR; ++q) {
+      const int it = tid + q * TC_THREADS;
+      const int rq = (it & 31) * 4, kc = (it >> 5) * EPC;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) put_group<X3>(t0, t1, tile_off<X3>(rq + i, kc), v + (q * 4 + i) * EPC);
     }
   }
 }
@@ -328,12 +365,15 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const GemmArgs g) {
     unsigned char* sB = sA + STAGE_BYTES / Md::TILES * (X3 ? 2 : 1);  // B (hi)
     unsigned char* sAl = sA + 4 * SUB_BYTES;                       // A lo (TF32 only)
     unsigned char* sBl = sB + 4 * SUB_BYTES;                       // B lo (TF32 only)
-    // the MMAs that read this buffer two iterations ago must be complete
-    if (it >= 2 && !failed && !mbar_wait(&s_mma_done[st], (uint32_t)((it - 2) >> 1) & 1u)) failed = true;
     const int k0 = kb + it * TK;
-    // K beyond this split's chunk reads as zero
-    stage_operand<X3, true>(g, sA, sAl, m0, k0, ke, tid);
-    stage_operand<X3, false>(g, sB, sBl, n0, k0, ke, tid);
+    // K beyond this split's chunk reads as zero; loads first, then the wait for
+    // the MMAs that read this buffer two iterations ago, then the stores
+    float va[Stage<X3>::VN], vb[Stage<X3>::VN];
+    load_operand<X3, true>(g, m0, k0, ke, tid, va);
+    load_operand<X3, false>(g, n0, k0, ke, tid, vb);
+    if (it >= 2 && !failed && !mbar_wait(&s_mma_done[st], (uint32_t)((it - 2) >> 1) & 1u)) failed = true;
+    store_operand<X3, true>(g, sA, sAl, tid, va);
+    store_operand<X3, false>(g, sB, sBl, tid, vb);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic stores -> tensor-core reads
     tc_fence_before();
     __syncthreads();

@@ -20,8 +20,8 @@ def _cuda():
     yield
 
 
-def make_factor(d, r, k, dtype, seed):
-    f = bkfac.Factor(d, r, dtype)
+def make_factor(d, r, k, dtype, seed, flags=0):
+    f = bkfac.Factor(d, r, dtype, flags=flags)
     if k:
         Ut = synth.orthonormal_columns(d, k, seed)
         sig = np.sort(2.0 * np.exp(-np.linspace(0, 5, k)))[::-1].copy()
@@ -30,9 +30,10 @@ def make_factor(d, r, k, dtype, seed):
     return f, U.double().cpu().numpy(), s.cpu().numpy()
 
 
-def run_apply(oracle, dA, rA, kA, dG, rG, kG, dtype, lamA=0.1, lamG=0.05, flags=0, inplace=False, seed=1):
-    fA, UA, sA = make_factor(dA, rA, kA, dtype, seed)
-    fG, UG, sG = make_factor(dG, rG, kG, dtype, seed + 1)
+def run_apply(oracle, dA, rA, kA, dG, rG, kG, dtype, lamA=0.1, lamG=0.05, flags=0, inplace=False, seed=1,
+              fflags=0):
+    fA, UA, sA = make_factor(dA, rA, kA, dtype, seed, fflags)
+    fG, UG, sG = make_factor(dG, rG, kG, dtype, seed + 1, fflags)
     Gn = synth.gradient(dG, dA, seed + 2, 0)
     G = bkfac.grad_tensor(dG, dA, fA.torch_dtype)
     G.copy_(torch.from_numpy(Gn))
@@ -75,3 +76,9 @@ def test_apply_wide_layer_full_size(oracle):
     """One wide FC layer: G 4096 x 4097 FP32 with r_A = r_G = 256, lambda = 1e-2."""
     err = run_apply(oracle, 4097, 256, 256, 4096, 256, 256, bkfac.F32, lamA=1e-2, lamG=1e-2)
     print(f"wide-layer apply relative error {err:.2e}")
+
+
+def test_apply_wide_layer_tf32x3(oracle):
+    """The wide layer's apply with 3xTF32 tensor-core passes."""
+    err = run_apply(oracle, 4097, 256, 256, 4096, 256, 256, bkfac.F32, lamA=1e-2, lamG=1e-2, fflags=bkfac.FLAG_TF32X3)
+    print(f"wide-layer 3xTF32 apply relative error {err:.2e}")

@@ -54,7 +54,7 @@ def check_status():
     assert st == bkfac.OK, bkfac.strerror(st)
 
 
-def one_step_parity(oracle, d, r, n, dtype, rho=0.95, steps=4, alpha=1.5, seed=1, flags=0):
+def one_step_parity(oracle, d, r, n, dtype, rho=0.95, steps=4, alpha=1.5, seed=1, flags=0, orth=None):
     f = bkfac.Factor(d, r, dtype, flags=flags)
     dense = r + n >= d
     tol = TOL[dtype]
@@ -83,7 +83,7 @@ def one_step_parity(oracle, d, r, n, dtype, rho=0.95, steps=4, alpha=1.5, seed=1
         worst = max(worst, es, er)
         assert es < tol, (t, es)
         assert er < tol, (t, er)
-        assert orth_err(U2[s2 > 0]) < ORTH[dtype]
+        assert orth_err(U2[s2 > 0]) < (ORTH[dtype] if orth is None else orth)
     return f, worst
 
 
@@ -99,6 +99,15 @@ def test_update_f32_one_step(oracle, d, r, n):
 
 def test_update_f32_with_fp64_eigensolve(oracle):
     one_step_parity(oracle, 400, 32, 24, bkfac.F32, alpha=1.2, steps=3, flags=bkfac.FLAG_EIG_FP64)
+
+
+def test_update_f32_tf32x3_one_step(oracle):
+    """F32 factor with its tall-skinny products as 3xTF32 on the tensor cores."""
+    # U' = [U Q] V carries the products' ~1e-5 relative error: orthonormality to the
+    # path's tolerance rather than the SIMT FP32 level
+    _, worst = one_step_parity(oracle, 600, 48, 40, bkfac.F32, alpha=1.2, steps=3, flags=bkfac.FLAG_TF32X3,
+                               orth=1e-4)
+    print(f"3xTF32 one-step worst relative error {worst:.3e}")
 
 
 def test_update_mixed_one_step(oracle):
@@ -130,26 +139,43 @@ def test_init_keeps_rank_n_when_n_below_r(oracle):
 
 
 def test_trajectory_f64_small_factor(oracle):
-    """Small FP64 factor (d=512, r=64, n=32, rho=0.95, alpha=1.5), free-running for
-    20 steps on both sides."""
-    d, r, n, rho = 512, 64, 32, 0.95
-    f = bkfac.Factor(d, r, bkfac.F64)
-    X0 = synth.powerlaw_batch(d, n, 1.5, 1000, 0)
-    bkfac.bkfac_init(f, to_dev(X0, f))
-    Uo, so, info = oracle.init(X0, r)
-    k = info["r_new"]
-    min_gap = np.inf
-    for t in range(1, 21):
-        X = synth.powerlaw_batch(d, n, 1.5, 1000, t)
-        bkfac.bkfac_update(f, to_dev(X, f), rho)
-        Uo, so, info = oracle.update(Uo[:k], so[:k], k, X, rho, r)
+    """Small FP64 workload: A factor d=512, Gamma factor d=256, r=64, n=32,
+    rho=0.95, alpha=1.5, both free-running for 50 steps on each side from the
+    first batch's exact EVD; then (Gamma + 0.1 I)^-1 G (A + 0.1 I)^-1 for a
+    256 x 512 N(0, 1) gradient, compared with the oracle's application on its
+    own trajectory."""
+    r, n, rho, steps = 64, 32, 0.95, 50
+    sides = []
+    for d, seed in ((512, 1000), (256, 1001)):
+        f = bkfac.Factor(d, r, bkfac.F64)
+        X0 = synth.powerlaw_batch(d, n, 1.5, seed, 0)
+        bkfac.bkfac_init(f, to_dev(X0, f))
+        Uo, so, info = oracle.init(X0, r)
         k = info["r_new"]
-        min_gap = min(min_gap, truncation_gap(so, min(r, len(so) - 1)))
+        min_gap = np.inf
+        for t in range(1, steps + 1):
+            X = synth.powerlaw_batch(d, n, 1.5, seed, t)
+            bkfac.bkfac_update(f, to_dev(X, f), rho)
+            Uo, so, info = oracle.update(Uo[:k], so[:k], k, X, rho, r)
+            k = info["r_new"]
+            min_gap = min(min_gap, truncation_gap(so, min(r, len(so) - 1)))
+        check_status()
+        Ug, sg = gpu_state(f)
+        err = lowrank_rel_err(Ug, sg, Uo[:k], so[:k])
+        print(f"d={d}: trajectory error after {steps} steps {err:.3e} (min truncation gap {min_gap:.2e})")
+        assert err < 1e-9
+        sides.append((f, Uo[:k], so[:k]))
+    (fA, UA, sA), (fG, UG, sG) = sides
+    Gn = synth.gradient(256, 512, 1002, 0)
+    G = bkfac.grad_tensor(256, 512, torch.float64)
+    G.copy_(torch.from_numpy(Gn))
+    S = bkfac.grad_tensor(256, 512, torch.float64)
+    bkfac.bkfac_apply(fA, fG, 0.1, 0.1, G, S)
     check_status()
-    Ug, sg = gpu_state(f)
-    err = lowrank_rel_err(Ug, sg, Uo[:k], so[:k])
-    print(f"trajectory error after 20 steps {err:.3e} (min truncation gap {min_gap:.2e})")
-    assert err < 1e-9
+    So = oracle.apply(UA, sA, 0.1, UG, sG, 0.1, Gn)
+    ea = rel(S.cpu().numpy(), So)
+    print(f"apply after {steps} steps: relative error {ea:.3e}")
+    assert ea < 1e-9
 
 
 def test_update_in_span_drops_residual(oracle):
