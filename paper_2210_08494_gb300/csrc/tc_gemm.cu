@@ -244,8 +244,46 @@ __device__ __forceinline__ void load_operand(const GemmArgs& g, int r0, int k0, 
                                              float (&v)[Stage<X3>::VN]) {
   using S = Stage<X3>;
   constexpr int EPC = S::EPC, CH = S::CH;
+  constexpr int TK = TcMode<X3>::TK;
   const bool kmaj = IS_A ? g.a_kmaj : g.b_kmaj;
   const int R = IS_A ? g.M : g.N;
+  // interior block (all rows and K in range, inside one segment, vector-aligned):
+  // straight-line 16-byte loads from one base pointer, all issued back to back
+  {
+    const Seg sg = seg_of<IS_A>(g, min(k0, max(K - 1, 0)));
+    const bool interior = r0 + TM <= R && k0 + TK <= K && (k0 >= g.K0 || k0 + TK <= g.K0) && sg.vec &&
+                          (sg.k & 3) == 0;
+    if (interior) {
+      if (kmaj) {
+        const float* base = sg.p + (int64_t)r0 * sg.ld + sg.k;
+#pragma unroll
+        for (int q = 0; q < S::NK; ++q) {
+          const int it = tid + q * TC_THREADS;
+          const float4* src = reinterpret_cast<const float4*>(base + (int64_t)(it / CH) * sg.ld + (it % CH) * EPC);
+#pragma unroll
+          for (int h = 0; h < EPC / 4; ++h) {
+            const float4 x = __ldg(src + h);
+            v[q * EPC + 4 * h] = x.x; v[q * EPC + 4 * h + 1] = x.y;
+            v[q * EPC + 4 * h + 2] = x.z; v[q * EPC + 4 * h + 3] = x.w;
+          }
+        }
+      } else {
+        const float* base = sg.p + r0 + (int64_t)sg.k * sg.ld;
+#pragma unroll
+        for (int q = 0; q < S::NR; ++q) {
+          const int it = tid + q * TC_THREADS;
+          const int rq = (it & 31) * 4, kc = (it >> 5) * EPC;
+#pragma unroll
+          for (int e = 0; e < EPC; ++e) {
+            const float4 x = __ldg(reinterpret_cast<const float4*>(base + rq + (int64_t)(kc + e) * sg.ld));
+            v[(q * 4 + 0) * EPC + e] = x.x; v[(q * 4 + 1) * EPC + e] = x.y;
+            v[(q * 4 + 2) * EPC + e] = x.z; v[(q * 4 + 3) * EPC + e] = x.w;
+          }
+        }
+      }
+      return;
+    }
+  }
   if (kmaj) {
 #pragma unroll
     for (int q = 0; q < S::NK; ++q) {
@@ -438,37 +476,48 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const GemmArgs g) {
       const int64_t ldo = g.splits > 1 ? g.N : g.ldc;
       const bool vec_o = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) && (ldo & 3) == 0;
       const bool vec_d = with_d && ((reinterpret_cast<uintptr_t>(g.D) & 15u) == 0) && (g.ldd & 3) == 0;
-      for (int r = wid; r < TM; r += TC_THREADS / 32) {
-        const int m = m0 + r;
-        if (m >= g.M || n >= g.N) continue;
-        const float rsm = (g.splits == 1 && g.rs) ? (float)g.rs[m] : 1.f;
-        float o[4];
+      const bool full = n + 4 <= g.N;
+      // eight rows per warp at a time: their D rows are all in flight before use
+      constexpr int RB = 8, RS = TC_THREADS / 32;
+      for (int r0b = wid; r0b < TM; r0b += RB * RS) {
+        float4 dq[RB];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          o[j] = T[r * TLD + 4 * lane + j];
-          if (g.splits == 1) o[j] *= alpha * rsm * csv[j];
+        for (int u = 0; u < RB; ++u) {
+          const int m = m0 + r0b + u * RS;
+          dq[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (with_d && m < g.M && n < g.N) {
+            const float* drow = (const float*)g.D + (int64_t)m * g.ldd + n;
+            if (full && vec_d) {
+              dq[u] = __ldg(reinterpret_cast<const float4*>(drow));
+            } else {
+              dq[u].x = drow[0];
+              if (n + 1 < g.N) dq[u].y = drow[1];
+              if (n + 2 < g.N) dq[u].z = drow[2];
+              if (n + 3 < g.N) dq[u].w = drow[3];
+            }
+          }
         }
-        const bool full = n + 4 <= g.N;
-        if (with_d) {
-          const float* drow = (const float*)g.D + (int64_t)m * g.ldd + n;
-          float dv[4];
-          if (full && vec_d) {
-            const float4 q = __ldg(reinterpret_cast<const float4*>(drow));
-            dv[0] = q.x; dv[1] = q.y; dv[2] = q.z; dv[3] = q.w;
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+          const int r = r0b + u * RS, m = m0 + r;
+          if (m >= g.M || n >= g.N) continue;
+          const float rsm = (g.splits == 1 && g.rs) ? (float)g.rs[m] : 1.f;
+          const float dv[4] = {dq[u].x, dq[u].y, dq[u].z, dq[u].w};
+          float o[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            o[j] = T[r * TLD + 4 * lane + j];
+            if (g.splits == 1) o[j] *= alpha * rsm * csv[j];
+            if (with_d) o[j] += beta * dv[j] * dsv[j];
+          }
+          float* orow = out + (int64_t)m * ldo + n;
+          if (full && vec_o) {
+            *reinterpret_cast<float4*>(orow) = make_float4(o[0], o[1], o[2], o[3]);
           } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) dv[j] = n + j < g.N ? drow[j] : 0.f;
+            for (int j = 0; j < 4; ++j)
+              if (n + j < g.N) orow[j] = o[j];
           }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) o[j] += beta * dv[j] * dsv[j];
-        }
-        float* orow = out + (int64_t)m * ldo + n;
-        if (full && vec_o) {
-          *reinterpret_cast<float4*>(orow) = make_float4(o[0], o[1], o[2], o[3]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (n + j < g.N) orow[j] = o[j];
         }
       }
     } else {
