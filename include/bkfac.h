@@ -133,7 +133,12 @@ enum { BKFAC_OP_UPDATE = 0, BKFAC_OP_REORTH = 1 };
 
 /* Bytes of workspace bkfac_init / bkfac_update (op = BKFAC_OP_UPDATE, with
  * batch width n) or bkfac_reorth (op = BKFAC_OP_REORTH, n ignored) need for
- * factor f.  Returns 0 for invalid arguments. */
+ * factor f.  Returns 0 for invalid arguments and for shapes beyond the
+ * eigensolve's capacity at the full rank: its matrix (N = r + n rows and
+ * columns on the Brand path, d rows and r + n columns on the dense path, r x r
+ * for reorth) may have at most 1024 rows with an FP32 eigensolve (768 columns
+ * once there are more than 512 rows) and 512 rows with an FP64 one; the calls
+ * return BKFAC_EINVAL for such shapes. */
 size_t bkfac_workspace_size(const bkfac_factor* f, int n, int op);
 
 /* Bytes of workspace bkfac_apply needs for the factor pair (fA, fG). */

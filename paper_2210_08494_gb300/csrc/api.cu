@@ -526,9 +526,11 @@ int check_ws(void* ws, size_t ws_bytes, size_t need) {
   return BKFAC_OK;
 }
 
-bool jacobi_fits(int C, int b, int rows_pad, DType jt) {
+// the eigensolve holds every row of its columns: rows <= rows_pad (at most 1024
+// FP32 / 512 FP64 rows) and two blocks of b columns within 200 KB of shared memory
+bool jacobi_fits(int rows, int C, int b, int rows_pad, DType jt) {
   (void)C;
-  return jacobi_smem_bytes(b, rows_pad, jt) <= 200 * 1024;
+  return rows <= rows_pad && b <= 32 && jacobi_smem_bytes(b, rows_pad, jt) <= 200 * 1024;
 }
 
 int update_common(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, void* ws, size_t ws_bytes,
@@ -543,7 +545,7 @@ int update_common(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho
   UpdatePlan p = plan_update(f, n, k);
   p.total = cap.total;
   if (p.rows_pad > p.rows_cap || p.cols_pad > p.cols_cap) return BKFAC_EINVAL;
-  if (!jacobi_fits(p.C, p.b, p.rows_pad, p.pr.jt)) return BKFAC_EINVAL;
+  if (!jacobi_fits(p.dense ? f->d : p.N, p.C, p.b, p.rows_pad, p.pr.jt)) return BKFAC_EINVAL;
   if (p.N > 8192 || (!p.dense && n > 1024)) return BKFAC_EINVAL;
   int rc = check_ws(ws, ws_bytes, cap.total);
   if (rc) return rc;
@@ -592,9 +594,16 @@ size_t bkfac_workspace_size(const bkfac_factor* f, int n, int op) {
   if (!valid_factor(f)) return 0;
   if (op == BKFAC_OP_UPDATE) {
     if (n < 1) return 0;
-    return plan_update(f, n, f->r).total;
+    const UpdatePlan cap = plan_update(f, n, f->r);
+    // beyond the eigensolve's capacity at the full rank: no workspace size
+    if (!jacobi_fits(cap.dense ? f->d : cap.N, cap.C, cap.b, cap.rows_pad, cap.pr.jt)) return 0;
+    return cap.total;
   }
-  if (op == BKFAC_OP_REORTH) return plan_reorth(f, f->r).total;
+  if (op == BKFAC_OP_REORTH) {
+    const ReorthPlan cap = plan_reorth(f, f->r);
+    if (!jacobi_fits(f->r, cap.C, cap.b, cap.rows_pad, cap.pr.jt)) return 0;
+    return cap.total;
+  }
   return 0;
 }
 
@@ -623,7 +632,7 @@ int bkfac_reorth(bkfac_factor* f, void* ws, size_t ws_bytes, bkfac_stream_t stre
   int rc = check_ws(ws, ws_bytes, cap.total);
   if (rc) return rc;
   if (p.rows_pad > cap.rows_cap || p.cols_pad > cap.cols_cap) return BKFAC_EINVAL;
-  if (!jacobi_fits(p.C, p.b, p.rows_pad, p.pr.jt)) return BKFAC_EINVAL;
+  if (!jacobi_fits(k, p.C, p.b, p.rows_pad, p.pr.jt)) return BKFAC_EINVAL;
   const Prec& pr = p.pr;
   const int d = f->d;
   TraceScope _reorth_ts(PH_REORTH, s);

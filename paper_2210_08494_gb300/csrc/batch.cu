@@ -61,12 +61,16 @@ int join_into(bkfac_batch* b, cudaStream_t s, int count) {
   return BKFAC_OK;
 }
 
+// one-CTA-per-SM clusters of 16 that fit on the GPU at once
+constexpr int kClustersAtOnce = 152 / 16;
+
 int batch_update(bkfac_batch* b, const void* const* X_A, const int64_t* ldxA, const void* const* X_G,
                  const int64_t* ldxG, double rho, cudaStream_t s) {
   const int nf = 2 * b->nl;
   int rc = fork_from(b, s, nf);
   int first_err = BKFAC_OK;
   if (rc) return rc;
+  bkfac::jacobi_set_many_concurrent(nf > kClustersAtOnce);
   for (int i = 0; i < nf; ++i) {
     const int l = i / 2;
     const void* X = (i & 1) ? X_G[l] : X_A[l];
@@ -77,6 +81,7 @@ int batch_update(bkfac_batch* b, const void* const* X_A, const int64_t* ldxA, co
                        : bkfac_update(f, X, ld, b->n, rho, ws, b->ws_len[i], (bkfac_stream_t)b->streams[i]);
     if (rc && !first_err) first_err = rc;
   }
+  bkfac::jacobi_set_many_concurrent(false);
   rc = join_into(b, s, nf);  // always join, so the caller's stream waits for whatever was enqueued
   return first_err ? first_err : rc;
 }

@@ -169,6 +169,9 @@ struct JacobiBatch {
 };
 // probs: host array of nprob <= kMaxJacobiProblems problems sharing the cluster size C
 // (passed by value as a kernel parameter, so the launch can be captured in a graph)
+// while set (per host thread), launch_jacobi prefers the L2 block exchange: many
+// eigensolves are about to run concurrently (batch API)
+void jacobi_set_many_concurrent(bool on);
 int launch_jacobi(const JacobiProblem* probs, int nprob, int C, DType j_t, double tol, int max_sweeps,
                   cudaStream_t s);
 // explicit block-exchange mode (false: through L2, true: distributed shared memory)

@@ -257,8 +257,8 @@ __global__ void __launch_bounds__(256) splitk_reduce(const GemmArgs g) {
 // 16-byte and conflict-free), 16-byte global loads, two shared-memory stages
 // with the next tile prefetched into registers while the current one is used.
 // Requires 16-byte aligned operands with leading dimensions a multiple of 4
-// and a first K segment that is a multiple of the tile depth (checked by the
-// caller); edges are zero-filled.
+// and, when an operand is K-contiguous, a first K segment that is a multiple of
+// 4 (checked by the caller); edges are zero-filled.
 // ---------------------------------------------------------------------------
 constexpr int LBM = 128, LBN = 128, LBK = 8, LNT = 256;
 
@@ -449,7 +449,10 @@ bool large_ok(const GemmArgs& g) {
   auto al = [](const void* p) { return p == nullptr || ((uintptr_t)p % 16) == 0; };
   if (g.sym) return false;
   if ((int64_t)g.M * g.N < 128 * 128 * 8) return false;  // small outputs: the 64 x 64 kernel
-  if (g.K0 % LBK != 0 && g.K1 > 0) return false;
+  // a 4-wide load along K must stay inside one K segment and 16-byte aligned: the
+  // seam K0 a multiple of 4 when either operand is K-contiguous (M- and N-contiguous
+  // operands load one K index at a time)
+  if (g.K1 > 0 && (g.a_kmaj || g.b_kmaj) && g.K0 % 4 != 0) return false;
   if (!al(g.A0) || !al(g.A1) || !al(g.B0) || !al(g.B1)) return false;
   if (g.lda0 % 4 || g.ldb0 % 4 || (g.K1 > 0 && (g.lda1 % 4 || g.ldb1 % 4))) return false;
   return true;

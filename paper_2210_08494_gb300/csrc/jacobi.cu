@@ -848,12 +848,20 @@ void jacobi_plan(int rows, int cols, DType j_t, int* C_out, int* b_out, int* row
   jacobi_plan_with(rows, cols, j_t, b_max, C_out, b_out, rows_pad, cols_pad);
 }
 
+namespace {
+thread_local bool t_many_concurrent = false;
+}
+
+void jacobi_set_many_concurrent(bool on) { t_many_concurrent = on; }
+
 int launch_jacobi(const JacobiProblem* probs, int nprob, int C, DType j_t, double tol, int max_sweeps,
                   cudaStream_t s) {
-  // block exchange over distributed shared memory unless the tuning table says
-  // otherwise (it is used only where two buffers fit)
-  int b = 0, dsm = 1;
-  if (nprob > 0) tune_lookup(probs[0].rows, probs[0].cols, j_t, &b, &dsm);
+  // Block exchange over distributed shared memory (three buffers per CTA, one CTA
+  // per SM) unless the tuning table says otherwise.  While a batch enqueues more
+  // eigensolves than one-CTA-per-SM clusters fit on the GPU, the exchange goes
+  // through L2 instead: a third of the shared memory lets two clusters share SMs.
+  int b = 0, dsm = t_many_concurrent ? 0 : 1;
+  if (nprob > 0 && !t_many_concurrent) tune_lookup(probs[0].rows, probs[0].cols, j_t, &b, &dsm);
   return launch_jacobi_mode(probs, nprob, C, j_t, tol, max_sweeps, dsm != 0, s);
 }
 

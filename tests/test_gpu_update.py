@@ -115,6 +115,37 @@ def test_update_mixed_one_step(oracle):
     print(f"mixed one-step worst relative error {worst:.3e}")
 
 
+@pytest.mark.parametrize("d,r,n,dtype", [(300, 24, 1, bkfac.F32), (300, 1, 16, bkfac.F32), (64, 1, 1, bkfac.F64),
+                                          (129, 2, 3, bkfac.F64)])
+def test_update_edge_ranks(oracle, d, r, n, dtype):
+    """Degenerate shapes: a single new column per step, a rank-one factor."""
+    one_step_parity(oracle, d, r, n, dtype, steps=3)
+
+
+def test_update_largest_core(oracle):
+    """The largest Brand core the FP32 eigensolve holds: N = r + n = 768 (1024-row
+    padded columns, two 24-column blocks per CTA in 192 KB of shared memory, two
+    columns per warp per register block, 16-CTA cluster)."""
+    _, worst = one_step_parity(oracle, 2048, 384, 384, bkfac.F32, alpha=1.2, steps=1)
+    print(f"N = 768 core: worst relative error {worst:.3e}")
+
+
+def test_shapes_beyond_the_eigensolve_are_rejected():
+    """N = 1024 with FP32 (two 32-column blocks of 1024 rows exceed the shared
+    memory) and N = 640 with FP64 (more than 512 rows): no workspace size, and
+    the update itself returns BKFAC_EINVAL before any launch."""
+    for d, r, n, dtype in ((2048, 384, 640, bkfac.F32), (2048, 320, 320, bkfac.F64)):
+        f = bkfac.Factor(d, r, dtype)
+        assert bkfac.bkfac_workspace_size(f, n) == 0
+        f.load_state(torch.from_numpy(synth.orthonormal_columns(d, r, 5)).to(f.torch_dtype).cuda(),
+                     torch.ones(r, dtype=torch.float64).cuda())
+        X = bkfac.cols_tensor(n, d, f.torch_dtype)
+        with pytest.raises(bkfac.BkfacError) as e:
+            bkfac.bkfac_update(f, X, 0.95, ws=bkfac.workspace(1 << 20))
+        assert e.value.code == bkfac.EINVAL
+    assert bkfac.bkfac_status() == bkfac.OK
+
+
 @pytest.mark.parametrize("dtype", [bkfac.F64, bkfac.F32])
 def test_dense_path_small_factor(oracle, dtype):
     """r + n >= d (the 10-way output layer's Gamma): explicit K, exact EVD."""
