@@ -19,7 +19,8 @@ wraps it with ctypes.  Conventions of the wrappers (numpy, float64):
 
 Paper: "Brand New K-FACs" (arXiv 2210.08494).  The functions follow Sec. 3.1
 (Algorithm 4, B-KFAC), Sec. 2.3 (Algorithm 3, symmetric Brand update, and the
-core of Eq. (7)) and Algorithm 1 (damped inverse application, Eq. (4)).
+core of Eq. (7)), Algorithm 1 (damped inverse application, Eq. (4)) and
+Algorithm 8 (the inverse application on the thin gradient factors).
 
 Parity status: pinned by ``tests/test_oracle_pins.py`` (closed forms, LAPACK
 cross-checks on small inputs, Propositions 3.1/3.2/4.1/4.2).  The paper prints
@@ -69,8 +70,10 @@ def _bind(lib):
     lib.bko_update_dense.argtypes = upd
     lib.bko_reorth.argtypes = [I, I, dp, L, dp, dp, L, dp]
     lib.bko_apply.argtypes = [I, I, dp, L, dp, D, I, I, dp, L, dp, D, dp, L, dp, L, I]
+    lib.bko_apply_factored.argtypes = [I, I, dp, L, dp, D, I, I, dp, L, dp, D, I, dp, L, dp, L, dp, L, dp, L, D,
+                                       dp, L, I]
     for f in (lib.bko_jacobi_eig, lib.bko_qrcp, lib.bko_project, lib.bko_core, lib.bko_update,
-              lib.bko_update_dense, lib.bko_reorth, lib.bko_apply):
+              lib.bko_update_dense, lib.bko_reorth, lib.bko_apply, lib.bko_apply_factored):
         f.restype = ctypes.c_int
     return lib
 
@@ -248,6 +251,35 @@ def apply(UAt, sigA, lamA: float, UGt, sigG, lamG: float, G, continuation: bool 
                              _p(sigG) if kG else _p(one), float(lamG), _p(G), dA, _p(S), dA,
                              1 if continuation else 0), "apply")
     return S
+
+
+def apply_factored(UAt, sigA, lamA: float, UGt, sigG, lamG: float, XAt, XGt, alpha: float = 1.0,
+                   form_step: bool = True, continuation: bool = False):
+    """Linear inverse application (Algorithm 8) on the thin gradient factors.
+
+    XAt: (n, dA) -- the input columns A_f, one row per column; XGt: (n, dG) -- the
+    back-propagated columns G_f.  Returns (PAt, PGt, S): PA = (A + lamA I)^-1 A_f and
+    PG = (Gamma + lamG I)^-1 G_f in the same (n, d) layout, and the step
+    S = alpha * PG PA^T as a (dG, dA) row-major array (None unless form_step).
+    """
+    UAt, UGt, XAt, XGt = _f64(UAt), _f64(UGt), _f64(XAt), _f64(XGt)
+    sigA, sigG = _f64(sigA), _f64(sigG)
+    kA, dA = UAt.shape
+    kG, dG = UGt.shape
+    n = XAt.shape[0]
+    assert XAt.shape == (n, dA) and XGt.shape == (n, dG)
+    PA = np.zeros((max(n, 1), dA))
+    PG = np.zeros((max(n, 1), dG))
+    S = np.zeros((dG, dA)) if form_step else None
+    one = np.zeros(1)
+    XA = XAt if n else np.zeros((1, dA))
+    XG = XGt if n else np.zeros((1, dG))
+    _check(_load().bko_apply_factored(
+        dA, kA, _p(UAt) if kA else _p(np.zeros(dA)), dA, _p(sigA) if kA else _p(one), float(lamA),
+        dG, kG, _p(UGt) if kG else _p(np.zeros(dG)), dG, _p(sigG) if kG else _p(one), float(lamG),
+        n, _p(XA), dA, _p(XG), dG, _p(PA), dA, _p(PG), dG, float(alpha),
+        _p(S) if form_step else None, dA, 1 if continuation else 0), "apply_factored")
+    return PA[:n], PG[:n], S
 
 
 def set_threads(n: int) -> None:

@@ -36,6 +36,12 @@
  *     the left factor, in plain loops.  Optional spectrum continuation
  *     (Sec. 3.5.1): lam <- lam + min(sigma), sigma <- sigma - min(sigma).
  *
+ *   apply_factored (Algorithm 8, linear inverse application): for a weight
+ *     gradient alpha * G_f A_f^T given by its thin factors (the columns that
+ *     also feed the K-factor updates), the damped inverses act on the factors,
+ *     PA = (U_A C_A U_A^T + I/lam_A) A_f,  PG = (U_G C_G U_G^T + I/lam_G) G_f,
+ *     and the step is S = alpha * PG PA^T (formed only when asked for).
+ *
  *   reorth: the top eigenpairs of U diag(sigma) U^T restricted to span(U)
  *     (Householder QR of U, Jacobi on R diag(sigma) R^T); a no-op in exact
  *     arithmetic when U is orthonormal.
@@ -519,5 +525,63 @@ int bko_apply(int dA, int kA, const double* UA, long lduA, const double* sigA, d
     }
   }
   free(cA); free(cG); free(T); free(Y);
+  return BKO_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * Linear inverse application (Algorithm 8).  The gradient of an FC layer over a
+ * batch is alpha * G_f A_f^T, G_f (dG x n) the back-propagated columns and A_f
+ * (dA x n) the input columns -- the same matrices whose outer products build the
+ * EA K-factors.  Algorithm 8 applies the low-rank damped inverses to these thin
+ * factors, column by column,
+ *   PA = A_f / lam_A + U_A C_A U_A^T A_f,   PG = G_f / lam_G + U_G C_G U_G^T G_f,
+ * and forms the step S = alpha * PG PA^T (dG x dA, row-major) when S != NULL.
+ * A_f, G_f, PA, PG are column-major (ld >= d).  Optional spectrum continuation
+ * as in apply.
+ * ------------------------------------------------------------------------- */
+static void damped_columns(int d, int k, const double* U, long ldu, const double* coef, double l, int n,
+                           const double* X, long ldx, double* P, long ldp) {
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < n; ++j) {
+    const double* x = X + (size_t)j * ldx;
+    double* p = P + (size_t)j * ldp;
+    for (int i = 0; i < d; ++i) p[i] = x[i] / l;
+    for (int a = 0; a < k; ++a) {
+      const double* u = U + (size_t)a * ldu;
+      double s = 0.0;
+      for (int i = 0; i < d; ++i) s += u[i] * x[i];
+      s *= coef[a];
+      for (int i = 0; i < d; ++i) p[i] += s * u[i];
+    }
+  }
+}
+
+int bko_apply_factored(int dA, int kA, const double* UA, long lduA, const double* sigA, double lamA, int dG,
+                       int kG, const double* UG, long lduG, const double* sigG, double lamG, int n,
+                       const double* XA, long ldxa, const double* XG, long ldxg, double* PA, long ldpa,
+                       double* PG, long ldpg, double alpha, double* S, long lds, int cont) {
+  if (dA <= 0 || dG <= 0 || kA < 0 || kG < 0 || n < 0 || lduA < dA || lduG < dG || ldxa < dA || ldxg < dG ||
+      ldpa < dA || ldpg < dG || (S && lds < dA) || !(lamA > 0.0) || !(lamG > 0.0))
+    return BKO_EINVAL;
+  double* cA = (double*)malloc(sizeof(double) * (size_t)(kA > 0 ? kA : 1));
+  double* cG = (double*)malloc(sizeof(double) * (size_t)(kG > 0 ? kG : 1));
+  if (!cA || !cG) { free(cA); free(cG); return BKO_ENOMEM; }
+  double lA, lG;
+  damped_coeffs(kA, sigA, lamA, cont, cA, &lA);
+  damped_coeffs(kG, sigG, lamG, cont, cG, &lG);
+  damped_columns(dA, kA, UA, lduA, cA, lA, n, XA, ldxa, PA, ldpa);
+  damped_columns(dG, kG, UG, lduG, cG, lG, n, XG, ldxg, PG, ldpg);
+  if (S) {
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < dG; ++i) {
+      double* srow = S + (size_t)i * lds;
+      for (int j = 0; j < dA; ++j) {
+        double acc = 0.0;
+        for (int t = 0; t < n; ++t) acc += PG[(size_t)i + (size_t)t * ldpg] * PA[(size_t)j + (size_t)t * ldpa];
+        srow[j] = alpha * acc;
+      }
+    }
+  }
+  free(cA); free(cG);
   return BKO_OK;
 }

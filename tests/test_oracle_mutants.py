@@ -23,6 +23,9 @@ MUTANTS = [
     ("apply: damped coefficient misses -1/lam",
      "coef[i] = 1.0 / ((sigma[i] - shift) + l) - 1.0 / l;", "coef[i] = 1.0 / ((sigma[i] - shift) + l);"),
     ("eigenvalues sorted ascending", "(best < 0 || lam[i] > lam[best])", "(best < 0 || lam[i] < lam[best])"),
+    ("linear apply: damped column misses its x / lam term", "for (int i = 0; i < d; ++i) p[i] = x[i] / l;",
+     "for (int i = 0; i < d; ++i) p[i] = 0.0;"),
+    ("linear apply: the step's scale alpha dropped", "srow[j] = alpha * acc;", "srow[j] = acc;"),
     ("dense path: rho applied to X X^T instead of U S U^T",
      "K[(size_t)i + (size_t)j * d] = s + c * t;", "K[(size_t)i + (size_t)j * d] = s / rho + rho * c * t;"),
 ]

@@ -390,6 +390,52 @@ def test_apply_spectrum_continuation(oracle):
     assert rel(S, ref) < 1e-12
 
 
+@pytest.mark.parametrize("dA,kA,dG,kG,n", [(24, 5, 17, 4, 6), (40, 0, 12, 3, 3), (9, 9, 30, 0, 5), (15, 4, 11, 2, 1)])
+def test_apply_factored_vs_dense_solve(oracle, dA, kA, dG, kG, n):
+    """Algorithm 8: PA = (A + lA I)^-1 A_f and PG = (Gamma + lG I)^-1 G_f on the thin
+    factors, checked column by column against LAPACK solves with the dense
+    represented factors; S = alpha PG PA^T."""
+    UA, sA = low_rank_factor(dA, kA, 31) if kA else (np.zeros((0, dA)), np.zeros(0))
+    UG, sG = low_rank_factor(dG, kG, 32) if kG else (np.zeros((0, dG)), np.zeros(0))
+    XA = synth.powerlaw_batch(dA, n, 1.2, 33, 0)
+    XG = synth.powerlaw_batch(dG, n, 1.2, 34, 0)
+    lA, lG, alpha = 0.07, 0.02, 1.0 / n
+    PA, PG, S = oracle.apply_factored(UA, sA, lA, UG, sG, lG, XA, XG, alpha=alpha)
+    Arep = (dense(UA, sA) if kA else np.zeros((dA, dA))) + lA * np.eye(dA)
+    Grep = (dense(UG, sG) if kG else np.zeros((dG, dG))) + lG * np.eye(dG)
+    refA = np.linalg.solve(Arep, XA.T).T
+    refG = np.linalg.solve(Grep, XG.T).T
+    assert rel(PA, refA) < 1e-12 and rel(PG, refG) < 1e-12
+    assert rel(S, alpha * refG.T @ refA) < 1e-12
+
+
+def test_apply_factored_equals_dense_apply(oracle):
+    """Algorithm 8 and Algorithm 1 are the same operator on G = alpha G_f A_f^T:
+    (Gamma + lG)^-1 (G_f A_f^T) (A + lA)^-1 = [(Gamma + lG)^-1 G_f] [(A + lA)^-1 A_f]^T
+    (both damped factors are symmetric), with and without spectrum continuation."""
+    dA, dG, n = 33, 21, 7
+    UA, sA = low_rank_factor(dA, 6, 35)
+    UG, sG = low_rank_factor(dG, 5, 36)
+    XA = synth.powerlaw_batch(dA, n, 1.5, 37, 0)
+    XG = synth.powerlaw_batch(dG, n, 1.5, 38, 0)
+    alpha = 2.0 / n
+    for cont in (False, True):
+        _, _, S = oracle.apply_factored(UA, sA, 0.05, UG, sG, 0.3, XA, XG, alpha=alpha, continuation=cont)
+        Sd = oracle.apply(UA, sA, 0.05, UG, sG, 0.3, alpha * XG.T @ XA, continuation=cont)
+        assert rel(S, Sd) < 1e-12
+
+
+def test_apply_factored_without_step(oracle):
+    dA, dG, n = 12, 10, 3
+    UA, sA = low_rank_factor(dA, 3, 39)
+    UG, sG = low_rank_factor(dG, 2, 40)
+    XA = synth.powerlaw_batch(dA, n, 1.2, 41, 0)
+    XG = synth.powerlaw_batch(dG, n, 1.2, 42, 0)
+    PA, PG, S = oracle.apply_factored(UA, sA, 0.1, UG, sG, 0.1, XA, XG, form_step=False)
+    PA2, PG2, _ = oracle.apply_factored(UA, sA, 0.1, UG, sG, 0.1, XA, XG)
+    assert S is None and np.array_equal(PA, PA2) and np.array_equal(PG, PG2)
+
+
 # --------------------------------------------------------------------------- planted mistakes
 
 
