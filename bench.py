@@ -582,6 +582,47 @@ def run_gpu(args, world, rank, local):
 
     variants = {} if args.no_batched else {"plain_f32_tf32x3": plain_variant(bkfac.FLAG_TF32X3)}
 
+    # ---- the inverse application alone: Algorithm 1 on the dense gradient vs Algorithm 8 on the
+    # thin factors of the same layer (A_f 4097 x 256, G_f 4096 x 256; S = G_f-side x A_f-side / n)
+    def time_calls(fn, reps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda.synchronize()
+        for t in range(reps):
+            flush.zero_()
+            ev[t][0].record(stream)
+            fn(t)
+            ev[t][1].record(stream)
+        torch.cuda.synchronize()
+        if bkfac.bkfac_status() != bkfac.OK:
+            raise RuntimeError("apply timing: device status not OK")
+        return shard.max_over_ranks(float(sum(a.elapsed_time(b) for a, b in ev)), device=dev) / reps
+
+    PA = bkfac.cols_tensor(N, D_A, torch.float32, dev)
+    PG = bkfac.cols_tensor(N, D_G, torch.float32, dev)
+    xi = lambda t: 1 + t % (POOL_X - 1)  # noqa: E731
+    dense_apply = lambda t: bkfac.bkfac_apply(fA, fG, LAM, LAM, Gs[t % POOL_G], S)  # noqa: E731
+    fact_apply = lambda t: bkfac.bkfac_apply_factored(fA, fG, LAM, LAM, XA[xi(t)], XG[xi(t)], PA, PG,  # noqa: E731
+                                                      alpha=1.0 / N, S=S)
+    thin_apply = lambda t: bkfac.bkfac_apply_factored(fA, fG, LAM, LAM, XA[xi(t)], XG[xi(t)], PA, PG)  # noqa: E731
+    for fn in (dense_apply, fact_apply, thin_apply):
+        for t in range(args.warmup):
+            fn(t)
+    flops_dense = 4.0 * D_G * D_A * (R + R)
+    flops_thin = 4.0 * N * (R * D_A + R * D_G)
+    flops_fact = flops_thin + 2.0 * D_G * D_A * N
+    apply_lines = {}
+    for name, fn, flops, nbytes, path in (
+            ("dense_alg1", dense_apply, flops_dense, 2 * D_G * D_A * 4,
+             "Algorithm 1 on the dense 4096 x 4097 gradient (two passes over G)"),
+            ("factored_alg8", fact_apply, flops_fact, (N * (2 * D_A + 2 * D_G) + D_G * D_A) * 4,
+             "Algorithm 8 on the thin factors, step S = PG PA^T / n formed"),
+            ("factored_alg8_thin", thin_apply, flops_thin, N * (2 * D_A + 2 * D_G) * 4,
+             "Algorithm 8, preconditioned thin factors only (no S)")):
+        ms = time_calls(fn, max(args.steps, 3))
+        apply_lines[name] = {"value": 1000.0 / ms * world, "unit": "preconditioned-grads/s", "ms": ms,
+                             "gflop": flops / 1e9, "tflops": flops / (ms * 1e-3) / 1e12,
+                             "algorithmic_gbytes": nbytes / 1e9, "path": path, "parity_bound": 1e-4}
+
     batched = {} if args.no_batched else {
         "f32_graph": run_batched(args, bkfac, synth, torch, dev, seedA, seedG, bkfac.F32, flush),
         "mixed_bf16_graph": run_batched(args, bkfac, synth, torch, dev, seedA, seedG, bkfac.MIXED_BF16, flush),
@@ -608,6 +649,7 @@ def run_gpu(args, world, rank, local):
             "jacobi_sweeps": sweeps,
             "batched": batched,
             "variants": variants,
+            "apply": apply_lines,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -197,6 +197,37 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
                 int64_t ldg, void* S, int64_t lds, uint32_t flags, void* ws, size_t ws_bytes,
                 bkfac_stream_t stream);
 
+/* Linear inverse application (Algorithm 8): when a layer's weight gradient
+ * is alpha * G_f A_f^T -- G_f (d_out x n) the back-propagated columns and A_f
+ * (d_in x n) the input columns of the batch, the same matrices whose outer
+ * products feed the K-factor updates -- the damped inverses act on the thin
+ * factors instead of a dense gradient:
+ *   PA = (U_A C_A U_A^T + I/lam_A) A_f     (d_in x n)
+ *   PG = (U_G C_G U_G^T + I/lam_G) G_f     (d_out x n)
+ *   S  = alpha * PG PA^T                   (optional, d_out x d_in)
+ * with C and the complete-basis rule as in bkfac_apply; S equals bkfac_apply
+ * on G = alpha * G_f A_f^T.  Work is O(n r (d_in + d_out)) for PA and PG and
+ * 2 n d_in d_out for S; no dense gradient is read.
+ *   XA, XG  device, column-major d_in x n / d_out x n (a torch (n, d) row-major
+ *           tensor), leading dimensions ldxa >= d_in, ldxg >= d_out; 16-byte
+ *           aligned base and leading dimension (in bytes)
+ *   PA, PG  device outputs, same layouts and alignment (ldpa >= d_in,
+ *           ldpg >= d_out); PA == XA (PG == XG) in place is allowed when the
+ *           leading dimensions agree
+ *   alpha   scale of the step (1/n for a mean-reduced loss with unscaled
+ *           columns); ignored when S is NULL
+ *   S       device, d_out x d_in row-major, lds >= d_in, or NULL to return only
+ *           PA and PG; must not overlap XA, XG, PA or PG
+ *   ws      bkfac_apply_factored_workspace_size(fA, fG, n) bytes
+ *   flags   BKFAC_SPECTRUM_CONTINUATION or 0
+ * Returns BKFAC_EINVAL for n < 1, bad leading dimensions or alignment, or
+ * non-positive damping. */
+size_t bkfac_apply_factored_workspace_size(const bkfac_factor* fA, const bkfac_factor* fG, int n);
+int bkfac_apply_factored(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, double lamG, const void* XA,
+                         int64_t ldxa, const void* XG, int64_t ldxg, int n, void* PA, int64_t ldpa, void* PG,
+                         int64_t ldpg, double alpha, void* S, int64_t lds, uint32_t flags, void* ws,
+                         size_t ws_bytes, bkfac_stream_t stream);
+
 /* The damped inverse application without a caller workspace.  There is no
  * counterpart in the paper: this is an interface for callers that cannot
  * allocate device memory (code running under a stream capture that forbids

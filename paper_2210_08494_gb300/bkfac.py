@@ -80,6 +80,8 @@ def load(build_if_missing: bool = True):
             "bkfac_reorth": ([FP, P, S, P], I),
             "bkfac_apply": ([FP, FP, D, D, P, I64, P, I64, U32, P, S, P], I),
             "bkfac_apply_noalloc": ([FP, FP, D, D, P, I64, P, I64, U32, P], I),
+            "bkfac_apply_factored_workspace_size": ([FP, FP, I], S),
+            "bkfac_apply_factored": ([FP, FP, D, D, P, I64, P, I64, I, P, I64, P, I64, D, P, I64, U32, P, S, P], I),
             "bkfac_debug_offsets": ([FP, I, ctypes.POINTER(ctypes.c_int64)], I),
             "bkfac_batch_create": ([ctypes.POINTER(bkfac_layer_desc), I, I, I, ctypes.c_char_p], P),
             "bkfac_batch_get_factor": ([P, I, I, FP], I),
@@ -116,7 +118,8 @@ def exported_symbols():
               "bkfac_apply_workspace_size", "bkfac_init", "bkfac_update", "bkfac_reorth", "bkfac_apply",
               "bkfac_debug_offsets", "bkfac_batch_create", "bkfac_batch_get_factor", "bkfac_batch_update",
               "bkfac_batch_apply", "bkfac_batch_step_graph", "bkfac_batch_destroy", "bkfac_trace_enable",
-              "bkfac_trace_read", "bkfac_trace_phase_name", "bkfac_apply_noalloc", "bkfac_tune", "bkfac_batch_reorth"):
+              "bkfac_trace_read", "bkfac_trace_phase_name", "bkfac_apply_noalloc", "bkfac_tune", "bkfac_batch_reorth",
+              "bkfac_apply_factored_workspace_size", "bkfac_apply_factored"):
         if hasattr(lib, n):
             names.append(n)
     return names
@@ -274,6 +277,27 @@ def bkfac_apply(fA: Factor, fG: Factor, lamA: float, lamG: float, G: torch.Tenso
     _check(load().bkfac_apply(ctypes.byref(fA.desc), ctypes.byref(fG.desc), float(lamA), float(lamG), _ptr(G),
                               G.stride(0), _ptr(S), S.stride(0), int(flags), _ptr(ws), ws.numel(), _stream(stream)),
            "bkfac_apply")
+
+
+def bkfac_apply_factored(fA: Factor, fG: Factor, lamA: float, lamG: float, XA: torch.Tensor, XG: torch.Tensor,
+                         PA: torch.Tensor, PG: torch.Tensor, alpha: float = 1.0, S: torch.Tensor | None = None,
+                         flags: int = 0, ws: torch.Tensor | None = None, stream=None):
+    """Linear inverse application (Algorithm 8) on the thin gradient factors.
+
+    XA: (n, d_in) and XG: (n, d_out) column tensors (cols_tensor layout), PA / PG the
+    outputs in the same layouts (may be XA / XG); S: (d_out, d_in) or None."""
+    n = XA.shape[0]
+    if ws is None:
+        key = ("factored", id(fG), n)
+        if key not in fA._ws:
+            fA._ws[key] = workspace(load().bkfac_apply_factored_workspace_size(ctypes.byref(fA.desc),
+                                                                               ctypes.byref(fG.desc), n), fA.U.device)
+        ws = fA._ws[key]
+    _check(load().bkfac_apply_factored(
+        ctypes.byref(fA.desc), ctypes.byref(fG.desc), float(lamA), float(lamG), _ptr(XA), _cols_ld(XA), _ptr(XG),
+        _cols_ld(XG), n, _ptr(PA), _cols_ld(PA), _ptr(PG), _cols_ld(PG), float(alpha),
+        _ptr(S) if S is not None else None, S.stride(0) if S is not None else 0, int(flags), _ptr(ws), ws.numel(),
+        _stream(stream)), "bkfac_apply_factored")
 
 
 def bkfac_debug_offsets(f: Factor, n: int):

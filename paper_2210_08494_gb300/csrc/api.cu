@@ -238,6 +238,38 @@ ApplyPlan plan_apply(const bkfac_factor* fA, const bkfac_factor* fG, int kA, int
   return p;
 }
 
+// workspace of the linear inverse application (Algorithm 8) for n columns
+struct FactoredPlan {
+  Prec pr;
+  int64_t ldtA, ldtG;  // T_A (r_A x n), T_G (r_G x n), column-major
+  size_t o_TA, o_TG, o_part, o_cA, o_cG, o_cAo, o_cGo, o_alpha, o_bA, o_bG, total;
+  size_t part_bytes;
+};
+
+FactoredPlan plan_factored(const bkfac_factor* fA, const bkfac_factor* fG, int n) {
+  FactoredPlan p{};
+  p.pr = prec_of(fA);
+  p.pr.x3 = p.pr.x3 || prec_of(fG).x3;
+  const int rA = fA->r, rG = fG->r;
+  p.ldtA = std::max(rA, 1);
+  p.ldtG = std::max(rG, 1);
+  const size_t es = es_of(p.pr.t), aes = es_of(p.pr.acc);
+  Layout L;
+  p.o_TA = L.add((size_t)p.ldtA * n * es);
+  p.o_TG = L.add((size_t)p.ldtG * n * es);
+  p.part_bytes = partial_bytes(std::max(rA, rG), n, 0, aes);
+  p.o_part = L.add(p.part_bytes);
+  p.o_cA = L.add((size_t)rA * 8);
+  p.o_cG = L.add((size_t)rG * 8);
+  p.o_cAo = L.add((size_t)rA * 8);
+  p.o_cGo = L.add((size_t)rG * 8);
+  p.o_alpha = L.add(8);
+  p.o_bA = L.add(8);
+  p.o_bG = L.add(8);
+  p.total = L.total;
+  return p;
+}
+
 template <typename P>
 P* at(void* ws, size_t off) {
   return (P*)((char*)ws + off);
@@ -729,6 +761,8 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
   ca.cA_over = cAo;
   ca.cG_over = cGo;
   ca.alpha = alpha;
+  ca.betaA = nullptr;
+  ca.betaG = nullptr;
   PHASE(PH_COEFS, launch_apply_coefs(ca, s));
   // pass 1: T1 = G U_A (d_out x kA), T2 = diag(C_G / lamA') U_G^T G (kG x d_in, row-major)
   if (kA > 0) {
@@ -836,6 +870,139 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.beta_dev = alpha;
     g.beta = 1.0;
     PHASE(PH_APPLY2, gemm_run(g, pr.t, pr.acc, pr.t, s));
+  }
+  return BKFAC_OK;
+}
+
+size_t bkfac_apply_factored_workspace_size(const bkfac_factor* fA, const bkfac_factor* fG, int n) {
+  if (!valid_factor(fA) || !valid_factor(fG) || fA->dtype != fG->dtype || n < 1) return 0;
+  return plan_factored(fA, fG, n).total;
+}
+
+// Algorithm 8: the damped inverses on the thin factors, then (optionally) the step.
+//   T = diag(C) (U^T X)  (r_cur x n, split K over d);   P = beta X + U T  (d x n)
+//   S = alpha PG PA^T
+int bkfac_apply_factored(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, double lamG, const void* XA,
+                         int64_t ldxa, const void* XG, int64_t ldxg, int n, void* PA, int64_t ldpa, void* PG,
+                         int64_t ldpg, double alpha, void* S, int64_t lds, uint32_t flags, void* ws,
+                         size_t ws_bytes, bkfac_stream_t stream) {
+  if (!valid_factor(fA) || !valid_factor(fG) || fA->dtype != fG->dtype || n < 1) return BKFAC_EINVAL;
+  if (!(lamA > 0.0) || !(lamG > 0.0) || !std::isfinite(lamA) || !std::isfinite(lamG)) return BKFAC_EINVAL;
+  if ((flags & ~(uint32_t)BKFAC_SPECTRUM_CONTINUATION) != 0) return BKFAC_EINVAL;
+  const int dA = fA->d, dG = fG->d;
+  if (!XA || !XG || !PA || !PG || ldxa < dA || ldxg < dG || ldpa < dA || ldpg < dG) return BKFAC_EINVAL;
+  const size_t es = fA->dtype == BKFAC_F64 ? 8 : 4;
+  for (const void* ptr : {XA, XG, (const void*)PA, (const void*)PG})
+    if (((uintptr_t)ptr) % 16 != 0) return BKFAC_EINVAL;
+  for (int64_t ld : {ldxa, ldxg, ldpa, ldpg})
+    if ((ld * (int64_t)es) % 16 != 0) return BKFAC_EINVAL;
+  if ((PA == XA && ldpa != ldxa) || (PG == XG && ldpg != ldxg)) return BKFAC_EINVAL;
+  if (S && (lds < dA || !std::isfinite(alpha))) return BKFAC_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int kA = fA->r_cur, kG = fG->r_cur;
+  const FactoredPlan p = plan_factored(fA, fG, n);
+  int rc = check_ws(ws, ws_bytes, p.total);
+  if (rc) return rc;
+  const Prec& pr = p.pr;
+  ApplyCoefArgs ca;
+  ca.sigA = fA->sigma;
+  ca.kA = kA;
+  ca.sigG = fG->sigma;
+  ca.kG = kG;
+  ca.lamA = lamA;
+  ca.lamG = lamG;
+  ca.continuation = (flags & BKFAC_SPECTRUM_CONTINUATION) ? 1 : 0;
+  ca.completeA = kA == dA ? 1 : 0;
+  ca.completeG = kG == dG ? 1 : 0;
+  ca.cA = at<double>(ws, p.o_cA);
+  ca.cG = at<double>(ws, p.o_cG);
+  ca.cA_over = at<double>(ws, p.o_cAo);
+  ca.cG_over = at<double>(ws, p.o_cGo);
+  ca.alpha = at<double>(ws, p.o_alpha);
+  ca.betaA = at<double>(ws, p.o_bA);
+  ca.betaG = at<double>(ws, p.o_bG);
+  PHASE(PH_COEFS, launch_apply_coefs(ca, s));
+  struct Side {
+    const bkfac_factor* f;
+    int k;
+    const void* X;
+    int64_t ldx;
+    void* P;
+    int64_t ldp;
+    void* T;
+    int64_t ldt;
+    const double* c;
+    const double* beta;
+  };
+  const Side sides[2] = {
+      {fA, kA, XA, ldxa, PA, ldpa, at<void>(ws, p.o_TA), p.ldtA, ca.cA, ca.betaA},
+      {fG, kG, XG, ldxg, PG, ldpg, at<void>(ws, p.o_TG), p.ldtG, ca.cG, ca.betaG},
+  };
+  for (const Side& sd : sides) {
+    const int d = sd.f->d;
+    if (sd.k > 0) {
+      // T = diag(C) U^T X  (k x n, K = d)
+      GemmArgs g = gemm_base();
+      g.M = sd.k;
+      g.N = n;
+      g.K0 = d;
+      g.A0 = sd.f->U;
+      g.lda0 = sd.f->ldu;
+      g.a_kmaj = true;
+      g.B0 = sd.X;
+      g.ldb0 = sd.ldx;
+      g.b_kmaj = true;
+      g.round_bf16 = pr.bf16;
+      g.tf32x3 = pr.x3;
+      g.C = sd.T;
+      g.ldc = sd.ldt;
+      g.rs = sd.c;
+      g.splits = gemm_pick_splits(sd.k, n, d, 152);
+      g.partial = at<void>(ws, p.o_part);
+      g.partial_bytes = p.part_bytes;
+      PHASE(PH_FACT_THIN, gemm_run(g, pr.t, pr.acc, pr.t, s));
+    }
+    // P = U T + beta X  (d x n, K = k; the epilogue reads X(i, j) before writing P(i, j),
+    // so P may be X)
+    GemmArgs g = gemm_base();
+    g.M = d;
+    g.N = n;
+    g.K0 = sd.k;
+    g.A0 = sd.f->U;
+    g.lda0 = sd.f->ldu;
+    g.a_kmaj = false;
+    g.B0 = sd.T;
+    g.ldb0 = sd.ldt;
+    g.b_kmaj = true;
+    g.round_bf16 = pr.bf16;
+    g.tf32x3 = pr.x3;
+    g.C = sd.P;
+    g.ldc = sd.ldp;
+    g.D = sd.X;
+    g.ldd = sd.ldx;
+    g.beta = 1.0;
+    g.beta_dev = sd.beta;
+    PHASE(PH_FACT_THIN, gemm_run(g, pr.t, pr.acc, pr.t, s));
+  }
+  if (S) {
+    // S = alpha PG PA^T  (d_out x d_in row-major, K = n)
+    GemmArgs g = gemm_base();
+    g.M = dG;
+    g.N = dA;
+    g.K0 = n;
+    g.A0 = PG;
+    g.lda0 = ldpg;
+    g.a_kmaj = false;
+    g.B0 = PA;
+    g.ldb0 = ldpa;
+    g.b_kmaj = false;
+    g.round_bf16 = pr.bf16;
+    g.tf32x3 = pr.x3;
+    g.C = S;
+    g.ldc = lds;
+    g.c_rowmaj = true;
+    g.alpha = alpha;
+    PHASE(PH_FACT_STEP, gemm_run(g, pr.t, pr.acc, pr.t, s));
   }
   return BKFAC_OK;
 }

@@ -223,6 +223,8 @@ struct ApplyCoefArgs {
   double* cA_over;   // kA: C_A / lamG'
   double* cG_over;   // kG: C_G / lamA'
   double* alpha;     // 1: 1 / (lamA' lamG')
+  double* betaA;     // 1: the identity weight of the A side (1 / lamA', or 0 for a complete basis); may be null
+  double* betaG;     // 1: the same for the Gamma side; may be null
 };
 int launch_apply_coefs(const ApplyCoefArgs& a, cudaStream_t s);
 
@@ -231,7 +233,8 @@ int launch_apply_coefs(const ApplyCoefArgs& a, cudaStream_t s);
 // ---------------------------------------------------------------------------
 enum Phase {
   PH_COLNORM, PH_PROJ, PH_RESID, PH_GRAM, PH_CHOL, PH_TRINV, PH_TRMM, PH_CORE, PH_JACOBI, PH_SORT,
-  PH_ROTATE, PH_FINALIZE, PH_DENSE, PH_COEFS, PH_APPLY1, PH_APPLY_SMALL, PH_APPLY2, PH_REORTH, PH_COUNT
+  PH_ROTATE, PH_FINALIZE, PH_DENSE, PH_COEFS, PH_APPLY1, PH_APPLY_SMALL, PH_APPLY2, PH_REORTH, PH_FACT_THIN,
+  PH_FACT_STEP, PH_COUNT
 };
 class TraceScope {
  public:

@@ -265,13 +265,14 @@ __device__ __forceinline__ J warp_sum_spread(const J (&v)[K], int lane) {
 // product and compute that pair's rotation -- each group one pair, so the
 // angle arithmetic is issued once for all K pairs; the angles are then
 // broadcast and each pair whose cosine exceeds the tolerance is rotated.  a /
-// bn are the tracked squared norms of x / y, xs / ys the stamps (sweep of the
-// last rotation).  act bit i enables pair i.  Returns the rotated pairs as a
-// bit mask.
+// bn are the tracked squared norms of x / y; xf / yf have bit i set while x[i] /
+// y[i] is fresh (rotated in this or the previous sweep), and rotated columns
+// become fresh.  act bit i enables pair i.  Returns the rotated pairs as a bit
+// mask.
 template <typename J, int NV, int K, int SH>
 __device__ __forceinline__ unsigned step_pairs(Col<J, NV> (&x)[K], Col<J, NV> (&y)[K], J (&a)[K], J (&bn)[K],
-                                               int (&xs)[K], int (&ys)[K], unsigned act, int sweep, J tol2,
-                                               J tiny, int lane) {
+                                               unsigned& xf, unsigned& yf, unsigned act, J tol2, J tiny,
+                                               int lane) {
   if (act == 0) return 0;
   constexpr int GL = 32 / K;  // lanes per pair group
   J pd[K];
@@ -311,8 +312,8 @@ __device__ __forceinline__ unsigned step_pairs(Col<J, NV> (&x)[K], Col<J, NV> (&
       rotate_lane(x[i], y[j], si[i], ti[i]);
       a[i] -= gi[i];
       bn[j] += gi[i];
-      xs[i] = sweep;
-      ys[j] = sweep;
+      xf |= 1u << i;
+      yf |= 1u << j;
     }
   }
   return rot;
@@ -372,8 +373,8 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
     for (int st = 0; st < b - 1; ++st) {
       Col<J, NV> x[K], y[K];
       J a[K], bn[K];
-      int xs[K], ys[K], p0[K], p1[K];
-      unsigned act = 0;
+      int p0[K], p1[K];
+      unsigned act = 0, xf = 0, yf = 0;
 #pragma unroll
       for (int i = 0; i < K; ++i) {
         const int q = wid * K + i;  // pair q of this sub-step: block q / hb, slot q mod hb
@@ -384,11 +385,9 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
         y[i].load(col(p1[i]), lane);
         a[i] = s_nrm[p0[i]];
         bn[i] = s_nrm[p1[i]];
-        xs[i] = s_stamp[sidx(p0[i])];
-        ys[i] = s_stamp[sidx(p1[i])];
-        act |= (fresh(xs[i]) || fresh(ys[i])) ? (1u << i) : 0u;
+        act |= (fresh(s_stamp[sidx(p0[i])]) || fresh(s_stamp[sidx(p1[i])])) ? (1u << i) : 0u;
       }
-      const unsigned r = step_pairs<J, NV, K, 0>(x, y, a, bn, xs, ys, act, sweep, tol2, tiny, lane);
+      const unsigned r = step_pairs<J, NV, K, 0>(x, y, a, bn, xf, yf, act, tol2, tiny, lane);
 #pragma unroll
       for (int i = 0; i < K; ++i) {
         if ((r >> i) & 1u) {
@@ -409,56 +408,54 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
   {
     Col<J, NV> x[K];
     J a[K];
-    int xs[K];
+    unsigned xf = 0;  // bit i: x[i] is fresh
     const int xc = wid * K;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       x[i].load(col(xc + i), lane);
       a[i] = s_nrm[xc + i];
-      xs[i] = s_stamp[sidx(xc + i)];
+      xf |= fresh(s_stamp[sidx(xc + i)]) ? 1u << i : 0u;
     }
     unsigned xdirty = 0;
     int v = wid;
     for (int s = 0; s < G; ++s) {
       Col<J, NV> y[K];
       J bn[K];
-      int ys[K];
+      unsigned yf = 0;  // bit i: y[i] is fresh
       const int yc = b + v * K;
 #pragma unroll
       for (int i = 0; i < K; ++i) {
         bn[i] = s_nrm[yc + i];
-        ys[i] = s_stamp[sidx(yc + i)];
+        yf |= fresh(s_stamp[sidx(yc + i)]) ? 1u << i : 0u;
       }
       unsigned ydirty = 0;
-      bool any = false;
-#pragma unroll
-      for (int i = 0; i < K; ++i) any = any || fresh(xs[i]) || fresh(ys[i]);
+      const bool any = (xf | yf) != 0;
       if (any)
 #pragma unroll
         for (int i = 0; i < K; ++i) y[i].load(col(yc + i), lane);
       auto act_mask = [&](int sh) {
         unsigned m = 0;
 #pragma unroll
-        for (int i = 0; i < K; ++i) m |= (fresh(xs[i]) || fresh(ys[(i + sh) % K])) ? (1u << i) : 0u;
+        for (int i = 0; i < K; ++i) m |= (((xf >> i) | (yf >> ((i + sh) % K))) & 1u) << i;
         return m;
       };
       unsigned r = 0;
-      if (any) r = step_pairs<J, NV, K, 0>(x, y, a, bn, xs, ys, act_mask(0), sweep, tol2, tiny, lane);
+      if (any) r = step_pairs<J, NV, K, 0>(x, y, a, bn, xf, yf, act_mask(0), tol2, tiny, lane);
       xdirty |= r;
       ydirty |= y_mask<K, 0>(r);
       rot += __popc(r);
       if (K > 1) {
-        r = any ? step_pairs<J, NV, K, 1 % K>(x, y, a, bn, xs, ys, act_mask(1 % K), sweep, tol2, tiny, lane) : 0u;
+        r = any ? step_pairs<J, NV, K, 1 % K>(x, y, a, bn, xf, yf, act_mask(1 % K), tol2, tiny, lane) : 0u;
         xdirty |= r;
         ydirty |= y_mask<K, 1 % K>(r);
         rot += __popc(r);
       }
       if (K > 2) {
-        r = any ? step_pairs<J, NV, K, 2 % K>(x, y, a, bn, xs, ys, act_mask(2 % K), sweep, tol2, tiny, lane) : 0u;
+        r = any ? step_pairs<J, NV, K, 2 % K>(x, y, a, bn, xf, yf, act_mask(2 % K), tol2, tiny, lane) : 0u;
         xdirty |= r;
         ydirty |= y_mask<K, 2 % K>(r);
         rot += __popc(r);
-        r = any ? step_pairs<J, NV, K, 3 % K>(x, y, a, bn, xs, ys, act_mask(3 % K), sweep, tol2, tiny, lane) : 0u;
+        r = any ? step_pairs<J, NV, K, 3 % K>(x, y, a, bn, xf, yf, act_mask(3 % K), tol2, tiny, lane) : 0u;
         xdirty |= r;
         ydirty |= y_mask<K, 3 % K>(r);
         rot += __popc(r);
@@ -469,7 +466,7 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
           y[i].store(col(yc + i), lane);
           if (lane == 0) {
             s_nrm[yc + i] = bn[i];
-            s_stamp[sidx(yc + i)] = ys[i];
+            s_stamp[sidx(yc + i)] = sweep;
           }
         }
       }
@@ -482,7 +479,7 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
         x[i].store(col(xc + i), lane);
         if (lane == 0) {
           s_nrm[xc + i] = a[i];
-          s_stamp[sidx(xc + i)] = xs[i];
+          s_stamp[sidx(xc + i)] = sweep;
         }
       }
     }

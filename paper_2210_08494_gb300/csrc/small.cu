@@ -454,7 +454,11 @@ __global__ void __launch_bounds__(256) apply_coefs_kernel(const ApplyCoefArgs a)
     a.cG[i] = c;
     a.cG_over[i] = c * bA;
   }
-  if (threadIdx.x == 0) *a.alpha = bA * bG;
+  if (threadIdx.x == 0) {
+    *a.alpha = bA * bG;
+    if (a.betaA) *a.betaA = bA;
+    if (a.betaG) *a.betaG = bG;
+  }
 }
 
 }  // namespace

@@ -50,3 +50,33 @@ def test_host_side_calls_without_gpu():
     rc = lib.bkfac_update(ctypes.byref(f), ctypes.c_void_p(0x30000), 4128, 256, 0.95, ctypes.c_void_p(0x40000),
                           ws, None)
     assert rc == bkfac.EINVAL
+
+
+def test_factored_apply_host_checks_without_gpu():
+    """Workspace sizing and argument validation of the linear inverse application
+    (Algorithm 8); invalid calls return EINVAL before anything is enqueued."""
+    import ctypes
+
+    from paper_2210_08494_gb300 import bkfac
+
+    lib = bkfac.load()
+    fA = bkfac.bkfac_factor(4097, 256, 256, bkfac.F32, 0x10000, 4128, 0x20000, 0, 0, 0)
+    fG = bkfac.bkfac_factor(4096, 256, 256, bkfac.F32, 0x10000, 4096, 0x20000, 0, 0, 0)
+    ws = lib.bkfac_apply_factored_workspace_size(ctypes.byref(fA), ctypes.byref(fG), 256)
+    assert ws >= 2 * 256 * 256 * 4
+    assert lib.bkfac_apply_factored_workspace_size(ctypes.byref(fA), ctypes.byref(fG), 0) == 0
+    P = ctypes.c_void_p
+    args = dict(XA=P(0x30000), ldxa=4128, XG=P(0x50000), ldxg=4096, n=256, PA=P(0x70000), ldpa=4128,
+                PG=P(0x90000), ldpg=4096)
+
+    def call(**kw):
+        a = dict(args, **kw)
+        return lib.bkfac_apply_factored(ctypes.byref(fA), ctypes.byref(fG), 1e-2, 1e-2, a["XA"], a["ldxa"], a["XG"],
+                                        a["ldxg"], a["n"], a["PA"], a["ldpa"], a["PG"], a["ldpg"], 1.0, None, 0, 0,
+                                        P(0x100000), ws, None)
+
+    assert call(XA=P(0x30004)) == bkfac.EINVAL        # misaligned base
+    assert call(ldxa=4097) == bkfac.EINVAL            # leading dimension not 16-byte aligned
+    assert call(ldpg=4000) == bkfac.EINVAL            # ld < d
+    assert call(n=0) == bkfac.EINVAL
+    assert call(PA=P(0x30000), ldpa=4160) == bkfac.EINVAL  # in place with another ld
