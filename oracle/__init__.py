@@ -234,10 +234,12 @@ def reorth(Ut, sigma):
     return Uo, so
 
 
-def apply(UAt, sigA, lamA: float, UGt, sigG, lamG: float, G, continuation: bool = False):
+def apply(UAt, sigA, lamA: float, UGt, sigG, lamG: float, G, continuation: bool = False,
+          relative: bool = False):
     """S = (Gamma + lamG I)^-1 G (A + lamA I)^-1 with the low-rank factors (Algorithm 1).
 
     UAt: (kA, dA), UGt: (kG, dG), G: (dG, dA) row-major.  Returns S (dG, dA).
+    relative: lamA / lamG are multiples of each factor's largest eigenvalue.
     """
     UAt, UGt, G = _f64(UAt), _f64(UGt), _f64(G)
     sigA, sigG = _f64(sigA), _f64(sigG)
@@ -249,12 +251,12 @@ def apply(UAt, sigA, lamA: float, UGt, sigG, lamG: float, G, continuation: bool 
     _check(_load().bko_apply(dA, kA, _p(UAt) if kA else _p(np.zeros(dA)), dA, _p(sigA) if kA else _p(one),
                              float(lamA), dG, kG, _p(UGt) if kG else _p(np.zeros(dG)), dG,
                              _p(sigG) if kG else _p(one), float(lamG), _p(G), dA, _p(S), dA,
-                             1 if continuation else 0), "apply")
+                             (1 if continuation else 0) | (2 if relative else 0)), "apply")
     return S
 
 
 def apply_factored(UAt, sigA, lamA: float, UGt, sigG, lamG: float, XAt, XGt, alpha: float = 1.0,
-                   form_step: bool = True, continuation: bool = False):
+                   form_step: bool = True, continuation: bool = False, relative: bool = False):
     """Linear inverse application (Algorithm 8) on the thin gradient factors.
 
     XAt: (n, dA) -- the input columns A_f, one row per column; XGt: (n, dG) -- the
@@ -278,7 +280,7 @@ def apply_factored(UAt, sigA, lamA: float, UGt, sigG, lamG: float, XAt, XGt, alp
         dA, kA, _p(UAt) if kA else _p(np.zeros(dA)), dA, _p(sigA) if kA else _p(one), float(lamA),
         dG, kG, _p(UGt) if kG else _p(np.zeros(dG)), dG, _p(sigG) if kG else _p(one), float(lamG),
         n, _p(XA), dA, _p(XG), dG, _p(PA), dA, _p(PG), dG, float(alpha),
-        _p(S) if form_step else None, dA, 1 if continuation else 0), "apply_factored")
+        _p(S) if form_step else None, dA, (1 if continuation else 0) | (2 if relative else 0)), "apply_factored")
     return PA[:n], PG[:n], S
 
 

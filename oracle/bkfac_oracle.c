@@ -457,12 +457,22 @@ done:
  * Damped inverse application (Algorithm 1, inverse application; Eq. (4)):
  *   S = L_G G R_A,   L = I/lam + U C U^T,   C = diag(1/(sigma+lam) - 1/lam).
  * G and S are row-major dG x dA (ldg, lds >= dA); S may not alias G.
- * cont != 0 enables spectrum continuation (Sec. 3.5.1) over the kA / kG
- * stored modes.
+ * Option bits (opt):
+ *   1  spectrum continuation (Sec. 3.5.1) over the kA / kG stored modes;
+ *   2  relative damping (the damping schedule of the experiments, Sec. 4):
+ *      the given lam is a multiple phi of the largest eigenvalue of the
+ *      represented factor, lam = phi * max_i sigma_i, taken before the
+ *      continuation shift.
  * ------------------------------------------------------------------------- */
-static void damped_coeffs(int k, const double* sigma, double lam, int cont, double* coef, double* lam_eff) {
+static void damped_coeffs(int k, const double* sigma, double lam, int opt, double* coef, double* lam_eff) {
+  if ((opt & 2) && k > 0) {
+    double top = sigma[0];
+    for (int i = 1; i < k; ++i)
+      if (sigma[i] > top) top = sigma[i];
+    lam *= top;
+  }
   double shift = 0.0;
-  if (cont && k > 0) {
+  if ((opt & 1) && k > 0) {
     shift = sigma[0];
     for (int i = 1; i < k; ++i)
       if (sigma[i] < shift) shift = sigma[i];
@@ -476,7 +486,7 @@ int bko_apply(int dA, int kA, const double* UA, long lduA, const double* sigA, d
               const double* UG, long lduG, const double* sigG, double lamG, const double* G, long ldg,
               double* S, long lds, int cont) {
   if (dA <= 0 || dG <= 0 || kA < 0 || kG < 0 || lduA < dA || lduG < dG || ldg < dA || lds < dA ||
-      !(lamA > 0.0) || !(lamG > 0.0))
+      !(lamA > 0.0) || !(lamG > 0.0) || ((cont & 2) && (kA < 1 || kG < 1)))
     return BKO_EINVAL;
   double* cA = (double*)malloc(sizeof(double) * (size_t)(kA > 0 ? kA : 1));
   double* cG = (double*)malloc(sizeof(double) * (size_t)(kG > 0 ? kG : 1));
@@ -536,8 +546,7 @@ int bko_apply(int dA, int kA, const double* UA, long lduA, const double* sigA, d
  * factors, column by column,
  *   PA = A_f / lam_A + U_A C_A U_A^T A_f,   PG = G_f / lam_G + U_G C_G U_G^T G_f,
  * and forms the step S = alpha * PG PA^T (dG x dA, row-major) when S != NULL.
- * A_f, G_f, PA, PG are column-major (ld >= d).  Optional spectrum continuation
- * as in apply.
+ * A_f, G_f, PA, PG are column-major (ld >= d).  Option bits as in apply.
  * ------------------------------------------------------------------------- */
 static void damped_columns(int d, int k, const double* U, long ldu, const double* coef, double l, int n,
                            const double* X, long ldx, double* P, long ldp) {
@@ -561,7 +570,8 @@ int bko_apply_factored(int dA, int kA, const double* UA, long lduA, const double
                        const double* XA, long ldxa, const double* XG, long ldxg, double* PA, long ldpa,
                        double* PG, long ldpg, double alpha, double* S, long lds, int cont) {
   if (dA <= 0 || dG <= 0 || kA < 0 || kG < 0 || n < 0 || lduA < dA || lduG < dG || ldxa < dA || ldxg < dG ||
-      ldpa < dA || ldpg < dG || (S && lds < dA) || !(lamA > 0.0) || !(lamG > 0.0))
+      ldpa < dA || ldpg < dG || (S && lds < dA) || !(lamA > 0.0) || !(lamG > 0.0) ||
+      ((cont & 2) && (kA < 1 || kG < 1)))
     return BKO_EINVAL;
   double* cA = (double*)malloc(sizeof(double) * (size_t)(kA > 0 ? kA : 1));
   double* cG = (double*)malloc(sizeof(double) * (size_t)(kG > 0 ? kG : 1));

@@ -26,6 +26,8 @@ MUTANTS = [
     ("linear apply: damped column misses its x / lam term", "for (int i = 0; i < d; ++i) p[i] = x[i] / l;",
      "for (int i = 0; i < d; ++i) p[i] = 0.0;"),
     ("linear apply: the step's scale alpha dropped", "srow[j] = alpha * acc;", "srow[j] = acc;"),
+    ("relative damping scaled by the smallest eigenvalue", "if (sigma[i] > top) top = sigma[i];",
+     "if (sigma[i] < top) top = sigma[i];"),
     ("dense path: rho applied to X X^T instead of U S U^T",
      "K[(size_t)i + (size_t)j * d] = s + c * t;", "K[(size_t)i + (size_t)j * d] = s / rho + rho * c * t;"),
 ]

@@ -436,6 +436,32 @@ def test_apply_factored_without_step(oracle):
     assert S is None and np.array_equal(PA, PA2) and np.array_equal(PG, PG2)
 
 
+def test_apply_relative_damping(oracle):
+    """Damping relative to the largest eigenvalue (the schedule of the experiments,
+    lambda = lambda_max * phi): checked against LAPACK's largest eigenvalue of the
+    dense represented factors and dense solves, alone and with spectrum continuation,
+    for Algorithm 1 and Algorithm 8."""
+    dA, dG, n = 26, 18, 4
+    UA, sA = low_rank_factor(dA, 6, 43)
+    UG, sG = low_rank_factor(dG, 5, 44)
+    G = synth.gradient(dG, dA, 45, 0)
+    XA = synth.powerlaw_batch(dA, n, 1.2, 46, 0)
+    XG = synth.powerlaw_batch(dG, n, 1.2, 47, 0)
+    phiA, phiG = 0.1, 0.05
+    lmA = np.linalg.eigvalsh(dense(UA, sA)).max()
+    lmG = np.linalg.eigvalsh(dense(UG, sG)).max()
+    for cont in (False, True):
+        mA, mG = (sA.min(), sG.min()) if cont else (0.0, 0.0)
+        Arep = dense(UA, sA - mA) + (phiA * lmA + mA) * np.eye(dA)
+        Grep = dense(UG, sG - mG) + (phiG * lmG + mG) * np.eye(dG)
+        S = oracle.apply(UA, sA, phiA, UG, sG, phiG, G, continuation=cont, relative=True)
+        assert rel(S, np.linalg.solve(Grep, G) @ np.linalg.inv(Arep)) < 1e-12
+        PA, PG, _ = oracle.apply_factored(UA, sA, phiA, UG, sG, phiG, XA, XG, form_step=False, continuation=cont,
+                                          relative=True)
+        assert rel(PA, np.linalg.solve(Arep, XA.T).T) < 1e-12
+        assert rel(PG, np.linalg.solve(Grep, XG.T).T) < 1e-12
+
+
 # --------------------------------------------------------------------------- planted mistakes
 
 
