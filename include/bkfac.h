@@ -83,24 +83,38 @@ enum {
                                          3xTF32 (hi/lo split, FP32 accumulation; relative error of a
                                          product ~1e-5 at K = 4096 instead of ~1e-7); the apply takes
                                          it when either factor carries it */
+#define BKFAC_FLAG_KEEP_RN (1u << 2)  /* truncate just before the next update instead of just after
+                                         this one (the order of Algorithm 4): after an update the
+                                         factor keeps up to r + r_extra modes, so the inverse
+                                         applications use the rank-(r + n) representation; the next
+                                         update starts from the leading r of them */
 
 /* ---- apply flags -------------------------------------------------------- */
 #define BKFAC_SPECTRUM_CONTINUATION (1u << 0) /* Sec. 3.5.1: lam += min sigma, sigma -= min sigma */
+#define BKFAC_DAMPING_RELATIVE (1u << 1)      /* the damping schedule of the experiments (Sec. 4): lam_A,
+                                                 lam_G are multiples phi of each factor's largest stored
+                                                 eigenvalue, lambda = phi * max sigma (before any
+                                                 continuation shift); needs r_cur >= 1 on both factors */
 
 /* ---- the low-rank factor state (Sec. 3.1: U~ in R^{d x r}, D~ diagonal) --
  * All buffers are caller-owned device memory.
  *   d      factor size (d_in + 1 for the forward factor A, d_out for Gamma)
  *   r      target rank, 1 <= r <= d
  *   r_cur  current rank (0 before bkfac_init); maintained by the library on
- *          the host: after an update r_cur = min(r, r_cur + n) (Brand path) or
- *          min(r, r_cur + n, d) (dense path).  Modes past the numerical rank
- *          hold sigma = 0 and may have a zero column in U.
+ *          the host: after an update r_cur = min(r_out, k + n) (Brand path) or
+ *          min(r_out, k + n, d) (dense path), with k = min(r_cur, r) the modes
+ *          the update starts from and r_out = r (or r + r_extra under
+ *          BKFAC_FLAG_KEEP_RN).  Modes past the numerical rank hold sigma = 0
+ *          and may have a zero column in U.
  *   dtype  BKFAC_F64 (U is double) or BKFAC_F32 / BKFAC_MIXED_BF16 (U float)
- *   U      device, d x r column-major, leading dimension ldu
- *   sigma  device, r doubles, eigenvalues in descending order (zero past r_cur)
+ *   U      device, d x r_out column-major, leading dimension ldu
+ *   sigma  device, r_out doubles, eigenvalues in descending order (zero past r_cur)
  *   step   number of updates applied so far (host counter, incremented by
  *          bkfac_init / bkfac_update)
  *   flags  BKFAC_FLAG_* bits
+ *   r_extra  with BKFAC_FLAG_KEEP_RN: columns U and sigma hold beyond r (the
+ *          largest n the factor is updated with keeps all r + n modes);
+ *          ignored (0) otherwise
  * The dense path (explicit d x d factor, Jacobi on its Gram factor) is used
  * when r + n >= d, where the symmetric Brand update's precondition r + n < d
  * (Algorithm 3) fails. */
@@ -114,7 +128,7 @@ typedef struct bkfac_factor {
   double* sigma;
   int64_t step;
   uint32_t flags;
-  int32_t reserved;
+  int32_t r_extra;
 } bkfac_factor;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -192,7 +206,7 @@ int bkfac_reorth(bkfac_factor* f, void* ws, size_t ws_bytes, bkfac_stream_t stre
  *   S       device, same layout, lds >= d_in; S == G (in place) is allowed
  *           when lds == ldg
  *   lamA, lamG  damping, > 0
- *   flags   BKFAC_SPECTRUM_CONTINUATION or 0 */
+ *   flags   BKFAC_SPECTRUM_CONTINUATION, BKFAC_DAMPING_RELATIVE (either, both or 0) */
 int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, double lamG, const void* G,
                 int64_t ldg, void* S, int64_t lds, uint32_t flags, void* ws, size_t ws_bytes,
                 bkfac_stream_t stream);
@@ -219,7 +233,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
  *   S       device, d_out x d_in row-major, lds >= d_in, or NULL to return only
  *           PA and PG; must not overlap XA, XG, PA or PG
  *   ws      bkfac_apply_factored_workspace_size(fA, fG, n) bytes
- *   flags   BKFAC_SPECTRUM_CONTINUATION or 0
+ *   flags   as bkfac_apply
  * Returns BKFAC_EINVAL for n < 1, bad leading dimensions or alignment, or
  * non-positive damping. */
 size_t bkfac_apply_factored_workspace_size(const bkfac_factor* fA, const bkfac_factor* fG, int n);

@@ -25,7 +25,9 @@ F64, F32, MIXED_BF16 = 0, 1, 2
 OK, EINVAL, ENOTAPPLICABLE, ECHOL, ENOCONV, ENONFINITE, ETIMEOUT, ECUDA, EWORKSPACE, ENOMEM = range(10)
 FLAG_EIG_FP64 = 1
 FLAG_TF32X3 = 2
+FLAG_KEEP_RN = 4
 SPECTRUM_CONTINUATION = 1
+DAMPING_RELATIVE = 2
 OP_UPDATE, OP_REORTH = 0, 1
 
 _TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, MIXED_BF16: torch.float32}
@@ -34,7 +36,7 @@ _TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, MIXED_BF16: torch.float3
 class bkfac_factor(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("r", ctypes.c_int32), ("r_cur", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("U", ctypes.c_void_p), ("ldu", ctypes.c_int64), ("sigma", ctypes.c_void_p),
-                ("step", ctypes.c_int64), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+                ("step", ctypes.c_int64), ("flags", ctypes.c_uint32), ("r_extra", ctypes.c_int32)]
 
 
 class bkfac_layer_desc(ctypes.Structure):
@@ -181,13 +183,14 @@ class Factor:
     """Device state of one K-factor: U (d x r column-major, stored as an (r, ldu)
     tensor), sigma (r doubles) and the C descriptor the library updates."""
 
-    def __init__(self, d: int, r: int, dtype: int = F32, device="cuda", flags: int = 0):
+    def __init__(self, d: int, r: int, dtype: int = F32, device="cuda", flags: int = 0, r_extra: int = 0):
         self.d, self.r, self.dtype = int(d), int(r), int(dtype)
+        self.r_extra = int(r_extra) if (int(flags) & FLAG_KEEP_RN) else 0
         tdt = _TORCH_DTYPE[self.dtype]
-        self.U = cols_tensor(self.r, self.d, tdt, device)
-        self.sigma = torch.zeros(self.r, dtype=torch.float64, device=device)
+        self.U = cols_tensor(self.r + self.r_extra, self.d, tdt, device)
+        self.sigma = torch.zeros(self.r + self.r_extra, dtype=torch.float64, device=device)
         self.desc = bkfac_factor(self.d, self.r, 0, self.dtype, self.U.data_ptr(), _cols_ld(self.U),
-                                 self.sigma.data_ptr(), 0, int(flags), 0)
+                                 self.sigma.data_ptr(), 0, int(flags), self.r_extra)
         self._ws = {}
 
     @property

@@ -35,8 +35,12 @@ struct Layout {
   }
 };
 
+int r_total(const bkfac_factor* f) { return factor_r_total(f); }
+
 bool valid_factor(const bkfac_factor* f) {
-  if (!f || f->d < 1 || f->r < 1 || f->r > f->d || f->r_cur < 0 || f->r_cur > f->r) return false;
+  if (!f || f->d < 1 || f->r < 1 || f->r > f->d || f->r_cur < 0) return false;
+  if ((f->flags & BKFAC_FLAG_KEEP_RN) && f->r_extra < 0) return false;
+  if (f->r_cur > r_total(f)) return false;
   if (f->dtype != BKFAC_F64 && f->dtype != BKFAC_F32 && f->dtype != BKFAC_MIXED_BF16) return false;
   if (!f->U || !f->sigma || f->ldu < f->d) return false;
   const size_t es = f->dtype == BKFAC_F64 ? 8 : 4;
@@ -107,7 +111,7 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
   int rows_cap, cols_cap;
   if (p.dense) {
     p.N = k + n;
-    p.r_new = std::min(std::min(f->r, k + n), f->d);
+    p.r_new = std::min(std::min(r_total(f), k + n), f->d);
     jacobi_plan(f->d, k + n, p.pr.jt, &p.C, &p.b, &p.rows_pad, &p.cols_pad);
     int C2, b2, rp2, cp2;
     jacobi_plan(f->d, f->r + n, p.pr.jt, &C2, &b2, &rp2, &cp2);
@@ -121,7 +125,7 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
   } else {
     const int kmax = f->r, Nmax = f->r + n;
     p.N = k + n;
-    p.r_new = std::min(f->r, k + n);
+    p.r_new = std::min(r_total(f), k + n);
     p.ldm = std::max(kmax, 1);
     p.ldv = round_up(Nmax, 4);
     jacobi_plan(p.N, p.N, p.pr.jt, &p.C, &p.b, &p.rows_pad, &p.cols_pad);
@@ -146,8 +150,8 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
     p.o_L = L.add((size_t)rows_cap * cols_cap * jes);
     p.o_cn = L.add((size_t)cols_cap * 8);
     p.o_lam = L.add((size_t)cols_cap * 8);
-    p.o_V = L.add((size_t)p.ldv * f->r * es);
-    p.o_Un = L.add((size_t)p.ldq * f->r * es);
+    p.o_V = L.add((size_t)p.ldv * r_total(f) * es);
+    p.o_Un = L.add((size_t)p.ldq * r_total(f) * es);
     p.o_sw = L.add(256);
     p.o_st = L.add((size_t)cols_cap * 4);
     p.o_flag = L.add(16);
@@ -173,7 +177,7 @@ ReorthPlan plan_reorth(const bkfac_factor* f, int k) {
   p.d = f->d;
   p.k = k;
   p.ldq = ld_of(f->d);
-  const int kmax = f->r;
+  const int kmax = r_total(f);
   p.ldv = round_up(std::max(kmax, 1), 4);
   const size_t es = es_of(p.pr.t), jes = es_of(p.pr.jt);
   jacobi_plan(std::max(k, 1), std::max(k, 1), p.pr.jt, &p.C, &p.b, &p.rows_pad, &p.cols_pad);
@@ -215,7 +219,7 @@ ApplyPlan plan_apply(const bkfac_factor* fA, const bkfac_factor* fG, int kA, int
   p.dG = fG->d;
   p.kA = kA;
   p.kG = kG;
-  const int rA = fA->r, rG = fG->r;
+  const int rA = r_total(fA), rG = r_total(fG);
   p.ld1 = ld_of(p.dG);  // T1, W1: d_out x r_A column-major
   p.ld2 = ld_of(p.dA);  // T2: r_G x d_in row-major
   p.ldw = std::max(rG, 1);
@@ -250,7 +254,7 @@ FactoredPlan plan_factored(const bkfac_factor* fA, const bkfac_factor* fG, int n
   FactoredPlan p{};
   p.pr = prec_of(fA);
   p.pr.x3 = p.pr.x3 || prec_of(fG).x3;
-  const int rA = fA->r, rG = fG->r;
+  const int rA = r_total(fA), rG = r_total(fG);
   p.ldtA = std::max(rA, 1);
   p.ldtG = std::max(rG, 1);
   const size_t es = es_of(p.pr.t), aes = es_of(p.pr.acc);
@@ -399,14 +403,14 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     so.V = f->U;
     so.ldv = f->ldu;
     so.sig = f->sigma;
-    so.r_sig = f->r;
+    so.r_sig = r_total(f);
     so.lam_sorted = at<double>(ws, p.o_lam);
     so.colnorm2 = a.colnorm2;
     so.cols_pad = p.cols_pad;
     PHASE(PH_SORT, launch_sort_output(so, pr.jt, pr.t, s));
     // columns past r_new are cleared so U holds no stale modes
-    if (p.r_new < f->r) {
-      PHASE(PH_FINALIZE, launch_finalize(f->U, f->ldu, f->U, f->ldu, d, p.r_new, f->r, pr.t, s));
+    if (p.r_new < r_total(f)) {
+      PHASE(PH_FINALIZE, launch_finalize(f->U, f->ldu, f->U, f->ldu, d, p.r_new, r_total(f), pr.t, s));
     }
     return BKFAC_OK;
   }
@@ -519,7 +523,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   so.V = at<void>(ws, p.o_V);
   so.ldv = p.ldv;
   so.sig = f->sigma;
-  so.r_sig = f->r;
+  so.r_sig = r_total(f);
   so.lam_sorted = at<double>(ws, p.o_lam);
   so.colnorm2 = ca.colnorm2;
   so.cols_pad = p.cols_pad;
@@ -548,7 +552,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   g.partial = part;
   g.partial_bytes = p.part_bytes;
   PHASE(PH_ROTATE, gemm_run(g, pr.t, pr.acc, pr.t, s));
-  PHASE(PH_FINALIZE, launch_finalize(f->U, f->ldu, g.C, p.ldq, d, p.r_new, f->r, pr.t, s));
+  PHASE(PH_FINALIZE, launch_finalize(f->U, f->ldu, g.C, p.ldq, d, p.r_new, r_total(f), pr.t, s));
   return BKFAC_OK;
 }
 
@@ -572,7 +576,9 @@ int update_common(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho
   if (((uintptr_t)X) % 16 != 0 || (ldx * (int64_t)es) % 16 != 0) return BKFAC_EINVAL;
   if (!(rho >= 0.0 && rho < 1.0)) return BKFAC_EINVAL;
   if (!init && f->r_cur < 1) return BKFAC_EINVAL;
-  const int k = init ? 0 : f->r_cur;
+  // truncation to the leading r modes happens here, just before the update (with
+  // BKFAC_FLAG_KEEP_RN the factor may hold more after the previous one)
+  const int k = init ? 0 : std::min(f->r_cur, f->r);
   const UpdatePlan cap = plan_update(f, n, f->r);
   UpdatePlan p = plan_update(f, n, k);
   p.total = cap.total;
@@ -632,8 +638,8 @@ size_t bkfac_workspace_size(const bkfac_factor* f, int n, int op) {
     return cap.total;
   }
   if (op == BKFAC_OP_REORTH) {
-    const ReorthPlan cap = plan_reorth(f, f->r);
-    if (!jacobi_fits(f->r, cap.C, cap.b, cap.rows_pad, cap.pr.jt)) return 0;
+    const ReorthPlan cap = plan_reorth(f, r_total(f));
+    if (!jacobi_fits(r_total(f), cap.C, cap.b, cap.rows_pad, cap.pr.jt)) return 0;
     return cap.total;
   }
   return 0;
@@ -641,7 +647,7 @@ size_t bkfac_workspace_size(const bkfac_factor* f, int n, int op) {
 
 size_t bkfac_apply_workspace_size(const bkfac_factor* fA, const bkfac_factor* fG) {
   if (!valid_factor(fA) || !valid_factor(fG) || fA->dtype != fG->dtype) return 0;
-  return plan_apply(fA, fG, fA->r, fG->r).total;
+  return plan_apply(fA, fG, r_total(fA), r_total(fG)).total;
 }
 
 int bkfac_init(bkfac_factor* f, const void* X, int64_t ldx, int n, void* ws, size_t ws_bytes,
@@ -659,7 +665,7 @@ int bkfac_reorth(bkfac_factor* f, void* ws, size_t ws_bytes, bkfac_stream_t stre
   const int k = f->r_cur;
   if (k == 0) return BKFAC_OK;
   const cudaStream_t s = (cudaStream_t)stream;
-  const ReorthPlan cap = plan_reorth(f, f->r);
+  const ReorthPlan cap = plan_reorth(f, r_total(f));
   const ReorthPlan p = plan_reorth(f, k);
   int rc = check_ws(ws, ws_bytes, cap.total);
   if (rc) return rc;
@@ -699,7 +705,7 @@ int bkfac_reorth(bkfac_factor* f, void* ws, size_t ws_bytes, bkfac_stream_t stre
   so.V = at<void>(ws, cap.o_V);
   so.ldv = cap.ldv;
   so.sig = f->sigma;
-  so.r_sig = f->r;
+  so.r_sig = r_total(f);
   so.lam_sorted = at<double>(ws, cap.o_lam);
   so.colnorm2 = cn;
   so.cols_pad = p.cols_pad;
@@ -717,7 +723,7 @@ int bkfac_reorth(bkfac_factor* f, void* ws, size_t ws_bytes, bkfac_stream_t stre
   g.C = at<void>(ws, cap.o_Un);
   g.ldc = cap.ldq;
   BK_TRY(gemm_run(g, pr.t, pr.acc, pr.t, s));
-  BK_TRY(launch_finalize(f->U, f->ldu, g.C, cap.ldq, d, k, f->r, pr.t, s));
+  BK_TRY(launch_finalize(f->U, f->ldu, g.C, cap.ldq, d, k, r_total(f), pr.t, s));
   return BKFAC_OK;
 }
 
@@ -727,11 +733,12 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
   if (!valid_factor(fA) || !valid_factor(fG) || fA->dtype != fG->dtype) return BKFAC_EINVAL;
   if (!G || !S || ldg < fA->d || lds < fA->d) return BKFAC_EINVAL;
   if (!(lamA > 0.0) || !(lamG > 0.0) || !std::isfinite(lamA) || !std::isfinite(lamG)) return BKFAC_EINVAL;
-  if ((flags & ~(uint32_t)BKFAC_SPECTRUM_CONTINUATION) != 0) return BKFAC_EINVAL;
+  if ((flags & ~(uint32_t)(BKFAC_SPECTRUM_CONTINUATION | BKFAC_DAMPING_RELATIVE)) != 0) return BKFAC_EINVAL;
+  if ((flags & BKFAC_DAMPING_RELATIVE) && (fA->r_cur < 1 || fG->r_cur < 1)) return BKFAC_EINVAL;
   if (S == G && lds != ldg) return BKFAC_EINVAL;
   const cudaStream_t s = (cudaStream_t)stream;
   const int kA = fA->r_cur, kG = fG->r_cur;
-  const ApplyPlan cap = plan_apply(fA, fG, fA->r, fG->r);
+  const ApplyPlan cap = plan_apply(fA, fG, r_total(fA), r_total(fG));
   const ApplyPlan p = plan_apply(fA, fG, kA, kG);
   int rc = check_ws(ws, ws_bytes, cap.total);
   if (rc) return rc;
@@ -754,6 +761,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
   ca.lamA = lamA;
   ca.lamG = lamG;
   ca.continuation = (flags & BKFAC_SPECTRUM_CONTINUATION) ? 1 : 0;
+  ca.relative = (flags & BKFAC_DAMPING_RELATIVE) ? 1 : 0;
   ca.completeA = kA == dA ? 1 : 0;
   ca.completeG = kG == dG ? 1 : 0;
   ca.cA = cA;
@@ -888,7 +896,8 @@ int bkfac_apply_factored(const bkfac_factor* fA, const bkfac_factor* fG, double 
                          size_t ws_bytes, bkfac_stream_t stream) {
   if (!valid_factor(fA) || !valid_factor(fG) || fA->dtype != fG->dtype || n < 1) return BKFAC_EINVAL;
   if (!(lamA > 0.0) || !(lamG > 0.0) || !std::isfinite(lamA) || !std::isfinite(lamG)) return BKFAC_EINVAL;
-  if ((flags & ~(uint32_t)BKFAC_SPECTRUM_CONTINUATION) != 0) return BKFAC_EINVAL;
+  if ((flags & ~(uint32_t)(BKFAC_SPECTRUM_CONTINUATION | BKFAC_DAMPING_RELATIVE)) != 0) return BKFAC_EINVAL;
+  if ((flags & BKFAC_DAMPING_RELATIVE) && (fA->r_cur < 1 || fG->r_cur < 1)) return BKFAC_EINVAL;
   const int dA = fA->d, dG = fG->d;
   if (!XA || !XG || !PA || !PG || ldxa < dA || ldxg < dG || ldpa < dA || ldpg < dG) return BKFAC_EINVAL;
   const size_t es = fA->dtype == BKFAC_F64 ? 8 : 4;
@@ -912,6 +921,7 @@ int bkfac_apply_factored(const bkfac_factor* fA, const bkfac_factor* fG, double 
   ca.lamA = lamA;
   ca.lamG = lamG;
   ca.continuation = (flags & BKFAC_SPECTRUM_CONTINUATION) ? 1 : 0;
+  ca.relative = (flags & BKFAC_DAMPING_RELATIVE) ? 1 : 0;
   ca.completeA = kA == dA ? 1 : 0;
   ca.completeG = kG == dG ? 1 : 0;
   ca.cA = at<double>(ws, p.o_cA);

@@ -9,6 +9,7 @@
 // the whole step (every update, then every apply) replays as a single graph
 // launch.
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -212,8 +213,9 @@ int bkfac_batch_step_graph(bkfac_batch* b, const void* const* X_A, const int64_t
   if (capture) {
     if (!X_A || !X_G || !ldxA || !ldxG || !G || !S || !ldg || !lds || !lamA || !lamG) return BKFAC_EINVAL;
     // the captured launch shapes depend on r_cur: only a steady rank replays identically
+    // (r, or min(r + r_extra, r + n, d) for a factor that keeps the rank-(r + n) modes)
     for (const auto& f : b->f)
-      if (f.r_cur != f.r) return BKFAC_EINVAL;
+      if (f.r_cur != std::min(std::min(bkfac::factor_r_total(&f), f.r + b->n), (int)f.d)) return BKFAC_EINVAL;
     if (s == nullptr) return BKFAC_EINVAL;  // the legacy stream cannot be captured
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);

@@ -9,6 +9,12 @@
 
 namespace bkfac {
 
+// modes a factor holds after an update: r, or r + r_extra when it keeps the
+// untruncated rank-(r + n) representation until the next update (BKFAC_FLAG_KEEP_RN)
+inline int factor_r_total(const bkfac_factor* f) {
+  return f->r + ((f->flags & BKFAC_FLAG_KEEP_RN) && f->r_extra > 0 ? f->r_extra : 0);
+}
+
 // ---------------------------------------------------------------------------
 // Device status word.  Kernels record the first error with atomicCAS and
 // never trap; bkfac_status() reads and clears it.
@@ -217,6 +223,7 @@ struct ApplyCoefArgs {
   int kG;
   double lamA, lamG;
   int continuation;
+  int relative;              // lamA / lamG are multiples of each factor's largest eigenvalue
   int completeA, completeG;  // r_cur == d: the basis spans R^d and the 1/lambda complement is empty
   double* cA;        // kA: C_A
   double* cG;        // kG: C_G

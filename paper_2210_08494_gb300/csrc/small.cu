@@ -424,20 +424,29 @@ __global__ void __launch_bounds__(256) finalize_kernel(T* U, int64_t ldu, const 
 
 // ---------------------------------------------------------------- apply coefficients
 __global__ void __launch_bounds__(256) apply_coefs_kernel(const ApplyCoefArgs a) {
-  __shared__ double smin[2];
+  __shared__ double smin[2], slam[2];
   if (threadIdx.x < 2) {
     const double* sg = threadIdx.x == 0 ? a.sigA : a.sigG;
     const int k = threadIdx.x == 0 ? a.kA : a.kG;
+    double lam = threadIdx.x == 0 ? a.lamA : a.lamG;
+    if (a.relative && k > 0) {
+      // lambda = phi * (largest eigenvalue of the represented factor)
+      double top = sg[0];
+      for (int i = 1; i < k; ++i) top = fmax(top, sg[i]);
+      lam *= top;
+      if (!(lam > 0.0)) report(BKFAC_ENONFINITE);
+    }
     double m = 0.0;
     if (a.continuation && k > 0) {
       m = sg[0];
       for (int i = 1; i < k; ++i) m = fmin(m, sg[i]);
     }
     smin[threadIdx.x] = m;
+    slam[threadIdx.x] = lam;
   }
   __syncthreads();
   const double shA = smin[0], shG = smin[1];
-  const double lA = a.lamA + shA, lG = a.lamG + shG;
+  const double lA = slam[0] + shA, lG = slam[1] + shG;
   // (U Sigma U^T + lambda I)^-1 = beta I + U C U^T with beta = 1/lambda' for the
   // complement of span(U) and C = (Sigma + lambda)^-1 - beta.  A complete basis
   // (r_cur = d) leaves no complement: beta = 0 and C = (Sigma + lambda)^-1, the same

@@ -42,7 +42,8 @@ def run_apply(oracle, dA, rA, kA, dG, rG, kG, dtype, lamA=0.1, lamG=0.05, flags=
     bkfac.bkfac_apply(fA, fG, lamA, lamG, G, S, flags=flags)
     st = bkfac.bkfac_status()
     assert st == bkfac.OK, bkfac.strerror(st)
-    So = oracle.apply(UA, sA, lamA, UG, sG, lamG, Gr, continuation=bool(flags & bkfac.SPECTRUM_CONTINUATION))
+    So = oracle.apply(UA, sA, lamA, UG, sG, lamG, Gr, continuation=bool(flags & bkfac.SPECTRUM_CONTINUATION),
+                      relative=bool(flags & bkfac.DAMPING_RELATIVE))
     err = rel(S.double().cpu().numpy(), So)
     assert err < TOL[dtype], err
     return err
@@ -60,6 +61,22 @@ def test_apply_small_layer_f64(oracle):
 
 def test_apply_spectrum_continuation(oracle):
     run_apply(oracle, 200, 12, 12, 90, 8, 8, bkfac.F64, flags=bkfac.SPECTRUM_CONTINUATION)
+
+
+@pytest.mark.parametrize("dtype", [bkfac.F64, bkfac.F32])
+def test_apply_relative_damping(oracle, dtype):
+    """lambda = phi * largest eigenvalue (the experiments' schedule), also with continuation."""
+    run_apply(oracle, 220, 14, 14, 96, 9, 9, dtype, lamA=0.1, lamG=0.05, flags=bkfac.DAMPING_RELATIVE)
+    run_apply(oracle, 220, 14, 14, 96, 9, 9, dtype, lamA=0.1, lamG=0.05,
+              flags=bkfac.DAMPING_RELATIVE | bkfac.SPECTRUM_CONTINUATION)
+
+
+def test_apply_relative_damping_needs_modes():
+    fA, _, _ = make_factor(50, 4, 0, bkfac.F64, 3)
+    fG, _, _ = make_factor(30, 4, 4, bkfac.F64, 4)
+    G = bkfac.grad_tensor(30, 50, torch.float64)
+    with pytest.raises(bkfac.BkfacError):
+        bkfac.bkfac_apply(fA, fG, 0.1, 0.1, G, G, flags=bkfac.DAMPING_RELATIVE)
 
 
 def test_apply_in_place(oracle):

@@ -37,7 +37,8 @@ def run_factored(oracle, dA, rA, kA, dG, rG, kG, n, dtype, lamA=0.1, lamG=0.05, 
     st = bkfac.bkfac_status()
     assert st == bkfac.OK, bkfac.strerror(st)
     PAo, PGo, So = oracle.apply_factored(UA, sA, lamA, UG, sG, lamG, XAr, XGr, alpha=alpha, form_step=form_step,
-                                         continuation=bool(flags & bkfac.SPECTRUM_CONTINUATION))
+                                         continuation=bool(flags & bkfac.SPECTRUM_CONTINUATION),
+                                         relative=bool(flags & bkfac.DAMPING_RELATIVE))
     errs = [rel(PA.double().cpu().numpy(), PAo), rel(PG.double().cpu().numpy(), PGo)]
     if form_step:
         errs.append(rel(S.double().cpu().numpy(), So))
@@ -57,6 +58,11 @@ def test_factored_in_place_without_step(oracle):
 
 def test_factored_spectrum_continuation(oracle):
     run_factored(oracle, 150, 10, 10, 80, 6, 6, 9, bkfac.F64, flags=bkfac.SPECTRUM_CONTINUATION)
+
+
+def test_factored_relative_damping(oracle):
+    run_factored(oracle, 150, 10, 10, 80, 6, 6, 9, bkfac.F32, lamA=0.1, lamG=0.02,
+                 flags=bkfac.DAMPING_RELATIVE | bkfac.SPECTRUM_CONTINUATION)
 
 
 @pytest.mark.parametrize("kA,kG", [(0, 5), (7, 0), (3, 5)])
