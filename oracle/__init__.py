@@ -20,7 +20,9 @@ wraps it with ctypes.  Conventions of the wrappers (numpy, float64):
 Paper: "Brand New K-FACs" (arXiv 2210.08494).  The functions follow Sec. 3.1
 (Algorithm 4, B-KFAC), Sec. 2.3 (Algorithm 3, symmetric Brand update, and the
 core of Eq. (7)), Algorithm 1 (damped inverse application, Eq. (4)) and
-Algorithm 8 (the inverse application on the thin gradient factors).
+Algorithm 8 (the inverse application on the thin gradient factors), and the
+dense EA factor with Algorithms 5 and 6 (the RSVD overwrite of B-R-KFAC and
+the light correction of B-KFAC-C).
 
 Parity status: pinned by ``tests/test_oracle_pins.py`` (closed forms, LAPACK
 cross-checks on small inputs, Propositions 3.1/3.2/4.1/4.2).  The paper prints
@@ -72,8 +74,12 @@ def _bind(lib):
     lib.bko_apply.argtypes = [I, I, dp, L, dp, D, I, I, dp, L, dp, D, dp, L, dp, L, I]
     lib.bko_apply_factored.argtypes = [I, I, dp, L, dp, D, I, I, dp, L, dp, D, I, dp, L, dp, L, dp, L, dp, L, D,
                                        dp, L, I]
+    lib.bko_ea_update.argtypes = [I, dp, L, I, dp, L, D, I]
+    lib.bko_correct.argtypes = [I, I, dp, L, dp, dp, L, I, ip]
+    lib.bko_rsvd.argtypes = [I, I, I, dp, L, dp, L, I, dp, L, dp]
     for f in (lib.bko_jacobi_eig, lib.bko_qrcp, lib.bko_project, lib.bko_core, lib.bko_update,
-              lib.bko_update_dense, lib.bko_reorth, lib.bko_apply, lib.bko_apply_factored):
+              lib.bko_update_dense, lib.bko_reorth, lib.bko_apply, lib.bko_apply_factored, lib.bko_ea_update,
+              lib.bko_correct, lib.bko_rsvd):
         f.restype = ctypes.c_int
     return lib
 
@@ -282,6 +288,42 @@ def apply_factored(UAt, sigA, lamA: float, UGt, sigG, lamG: float, XAt, XGt, alp
         n, _p(XA), dA, _p(XG), dG, _p(PA), dA, _p(PG), dG, float(alpha),
         _p(S) if form_step else None, dA, (1 if continuation else 0) | (2 if relative else 0)), "apply_factored")
     return PA[:n], PG[:n], S
+
+
+def ea_update(M, Xt, rho: float, first: bool = False):
+    """Dense EA K-factor (Eq. (5)): returns rho M + (1 - rho)/n X X^T, or X X^T / n when
+    first.  M: (d, d) symmetric; Xt: (n, d) -- the batch, one row per column."""
+    Xt = _f64(Xt)
+    n, d = Xt.shape
+    Mo = np.array(M, dtype=np.float64, order="F", copy=True) if M is not None else np.zeros((d, d), order="F")
+    _check(_load().bko_ea_update(d, _p(Mo), d, n, _p(Xt), d, float(rho), 1 if first else 0), "ea_update")
+    return np.ascontiguousarray(Mo)
+
+
+def correct(Ut, sigma, M, idx):
+    """Light correction (Algorithm 6) of the representation (Ut (k, d), sigma) against the
+    dense factor M along the modes idx; returns (Ut, sigma) re-sorted by decreasing sigma."""
+    Ut = np.array(_f64(Ut), copy=True)
+    sigma = np.array(_f64(sigma), copy=True)
+    k, d = Ut.shape
+    Mf = np.asfortranarray(_f64(M))
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
+    _check(_load().bko_correct(d, k, _p(Ut) if k else _p(np.zeros(d)), d, _p(sigma) if k else _p(np.zeros(1)),
+                               _p(Mf), d, len(ix), ix.ctypes.data_as(ctypes.POINTER(ctypes.c_int))), "correct")
+    return Ut, sigma
+
+
+def rsvd(M, Omega_t, r: int, q: int):
+    """RSVD overwrite (Algorithm 5): the top-r eigenpairs of the dense factor M estimated from
+    the test matrix Omega (given as (l, d), one row per column) with q power iterations.
+    Returns (Ut (r, d), sigma (r))."""
+    Om = _f64(Omega_t)
+    l, d = Om.shape
+    Mf = np.asfortranarray(_f64(M))
+    Ut = np.zeros((r, d))
+    sigma = np.zeros(r)
+    _check(_load().bko_rsvd(d, r, l, _p(Mf), d, _p(Om), d, int(q), _p(Ut), d, _p(sigma)), "rsvd")
+    return Ut, sigma
 
 
 def set_threads(n: int) -> None:

@@ -42,6 +42,20 @@
  *     PA = (U_A C_A U_A^T + I/lam_A) A_f,  PG = (U_G C_G U_G^T + I/lam_G) G_f,
  *     and the step is S = alpha * PG PA^T (formed only when asked for).
  *
+ *   ea_update (Eq. (5) / (8)): the dense EA K-factor that B-R-KFAC and
+ *     B-KFAC-C keep beside the low-rank representation,
+ *     M <- rho M + (1 - rho)/n X X^T  (M = X X^T / n at the first step).
+ *
+ *   correct (Algorithm 6, the light correction of B-KFAC-C): for n_crc chosen
+ *     modes idx of the representation, M_S = U_s^T M U_s with U_s = U[:, idx],
+ *     M_S = W diag(lam) W^T, then U[:, idx] <- U_s W and sigma[idx] <- lam;
+ *     the modes are then re-sorted by decreasing sigma (stable).
+ *
+ *   rsvd (Algorithm 5's overwrite of B-R-KFAC): randomised range finder with
+ *     a given test matrix Omega (d x l, l = r + oversampling) and q power
+ *     iterations, Y = M Omega, then q times Q = orth(Y), Y = M Q; Q = orth(Y),
+ *     B = Q^T M Q = W diag(lam) W^T, U = Q W[:, :r], sigma = lam[:r].
+ *
  *   reorth: the top eigenpairs of U diag(sigma) U^T restricted to span(U)
  *     (Householder QR of U, Jacobi on R diag(sigma) R^T); a no-op in exact
  *     arithmetic when U is orthonormal.
@@ -594,4 +608,135 @@ int bko_apply_factored(int dA, int kA, const double* UA, long lduA, const double
   }
   free(cA); free(cG);
   return BKO_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * Dense EA K-factor (Eq. (5) / (8)) for B-R-KFAC and B-KFAC-C:
+ *   first != 0:  M = X X^T / n     (kappa(0) = 1)
+ *   otherwise:   M = rho M + (1 - rho)/n X X^T
+ * M is d x d column-major (ldm >= d), X is d x n (ldx >= d).
+ * ------------------------------------------------------------------------- */
+int bko_ea_update(int d, double* M, long ldm, int n, const double* X, long ldx, double rho, int first) {
+  if (d <= 0 || n <= 0 || ldm < d || ldx < d) return BKO_EINVAL;
+  const double c = first ? 1.0 / n : (1.0 - rho) / n;
+  const double keep = first ? 0.0 : rho;
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < d; ++j)
+    for (int i = 0; i < d; ++i) {
+      double s = 0.0;
+      for (int t = 0; t < n; ++t) s += AT(X, ldx, i, t) * AT(X, ldx, j, t);
+      AT(M, ldm, i, j) = keep * AT(M, ldm, i, j) + c * s;
+    }
+  return BKO_OK;
+}
+
+/* stable re-sort of k modes by decreasing sigma (columns of U move along) */
+static int sort_modes(int d, int k, double* U, long ldu, double* sigma) {
+  int* order = (int*)malloc(sizeof(int) * (size_t)(k > 0 ? k : 1));
+  double* Ut = (double*)malloc(sizeof(double) * (size_t)d * (size_t)(k > 0 ? k : 1));
+  double* st = (double*)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+  if (!order || !Ut || !st) { free(order); free(Ut); free(st); return BKO_ENOMEM; }
+  for (int i = 0; i < k; ++i) order[i] = i;
+  for (int i = 1; i < k; ++i) { /* insertion sort: stable */
+    const int v = order[i];
+    int j = i - 1;
+    while (j >= 0 && sigma[order[j]] < sigma[v]) { order[j + 1] = order[j]; --j; }
+    order[j + 1] = v;
+  }
+  for (int j = 0; j < k; ++j) {
+    st[j] = sigma[order[j]];
+    for (int i = 0; i < d; ++i) Ut[(size_t)i + (size_t)j * d] = AT(U, ldu, i, order[j]);
+  }
+  for (int j = 0; j < k; ++j) {
+    sigma[j] = st[j];
+    for (int i = 0; i < d; ++i) AT(U, ldu, i, j) = Ut[(size_t)i + (size_t)j * d];
+  }
+  free(order); free(Ut); free(st);
+  return BKO_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * Light correction of a B-KFAC representation (Algorithm 6).  U (d x k, ldu)
+ * and sigma (k) are corrected in place along the n_crc modes idx (distinct,
+ * in [0, k)), against the dense EA factor M (d x d, ldm).
+ * ------------------------------------------------------------------------- */
+int bko_correct(int d, int k, double* U, long ldu, double* sigma, const double* M, long ldm, int n_crc,
+                const int* idx) {
+  if (d <= 0 || k < 0 || ldu < d || ldm < d || n_crc < 0 || n_crc > k) return BKO_EINVAL;
+  for (int a = 0; a < n_crc; ++a) {
+    if (idx[a] < 0 || idx[a] >= k) return BKO_EINVAL;
+    for (int b = 0; b < a; ++b)
+      if (idx[a] == idx[b]) return BKO_EINVAL;
+  }
+  if (n_crc == 0) return BKO_OK;
+  double* Us = (double*)malloc(sizeof(double) * (size_t)d * (size_t)n_crc);
+  double* MU = (double*)malloc(sizeof(double) * (size_t)d * (size_t)n_crc);
+  double* Ms = (double*)malloc(sizeof(double) * (size_t)n_crc * (size_t)n_crc);
+  double* W = (double*)malloc(sizeof(double) * (size_t)n_crc * (size_t)n_crc);
+  double* lam = (double*)malloc(sizeof(double) * (size_t)n_crc);
+  double* Un = (double*)malloc(sizeof(double) * (size_t)d * (size_t)n_crc);
+  int rc = BKO_ENOMEM;
+  if (!Us || !MU || !Ms || !W || !lam || !Un) goto done;
+  for (int a = 0; a < n_crc; ++a)
+    for (int i = 0; i < d; ++i) Us[(size_t)i + (size_t)a * d] = AT(U, ldu, i, idx[a]);
+  mat_nn(d, n_crc, d, M, ldm, Us, d, MU, d);          /* M U_s */
+  mat_tn(n_crc, n_crc, d, Us, d, MU, d, Ms, n_crc);    /* M_S = U_s^T M U_s */
+  for (int j = 0; j < n_crc; ++j)                       /* exact symmetry */
+    for (int i = j + 1; i < n_crc; ++i) {
+      const double v = 0.5 * (Ms[(size_t)i + (size_t)j * n_crc] + Ms[(size_t)j + (size_t)i * n_crc]);
+      Ms[(size_t)i + (size_t)j * n_crc] = Ms[(size_t)j + (size_t)i * n_crc] = v;
+    }
+  rc = bko_jacobi_eig(n_crc, Ms, n_crc, lam, W, n_crc, 100, NULL);
+  if (rc) goto done;
+  mat_nn(d, n_crc, n_crc, Us, d, W, n_crc, Un, d);    /* U_s W */
+  for (int a = 0; a < n_crc; ++a) {
+    for (int i = 0; i < d; ++i) AT(U, ldu, i, idx[a]) = Un[(size_t)i + (size_t)a * d];
+    sigma[idx[a]] = lam[a];
+  }
+  rc = sort_modes(d, k, U, ldu, sigma);
+done:
+  free(Us); free(MU); free(Ms); free(W); free(lam); free(Un);
+  return rc;
+}
+
+/* ---------------------------------------------------------------------------
+ * RSVD overwrite of a B-KFAC representation (Algorithm 5): randomised range
+ * finder on the dense EA factor M (d x d) with the test matrix Omega (d x l,
+ * ldo >= d, r <= l <= d) and q power iterations; orthonormal bases by
+ * Householder QR (bko_qrcp without truncation).  Writes U (d x r) and sigma (r).
+ * ------------------------------------------------------------------------- */
+int bko_rsvd(int d, int r, int l, const double* M, long ldm, const double* Omega, long ldo, int q, double* U,
+             long ldu, double* sigma) {
+  if (d <= 0 || r < 1 || l < r || l > d || ldm < d || ldo < d || ldu < d || q < 0) return BKO_EINVAL;
+  double* Y = (double*)malloc(sizeof(double) * (size_t)d * (size_t)l);
+  double* Q = (double*)malloc(sizeof(double) * (size_t)d * (size_t)l);
+  double* Rt = (double*)malloc(sizeof(double) * (size_t)l * (size_t)l);
+  double* B = (double*)malloc(sizeof(double) * (size_t)l * (size_t)l);
+  double* W = (double*)malloc(sizeof(double) * (size_t)l * (size_t)l);
+  double* lam = (double*)malloc(sizeof(double) * (size_t)l);
+  int rc = BKO_ENOMEM, m = 0;
+  if (!Y || !Q || !Rt || !B || !W || !lam) goto done;
+  mat_nn(d, l, d, M, ldm, Omega, ldo, Y, d);           /* Y = M Omega */
+  for (int it = 0; it < q; ++it) {
+    rc = bko_qrcp(d, l, Y, d, 0.0, Q, d, Rt, l, &m);
+    if (rc) goto done;
+    mat_nn(d, l, d, M, ldm, Q, d, Y, d);               /* Y = M Q */
+  }
+  rc = bko_qrcp(d, l, Y, d, 0.0, Q, d, Rt, l, &m);
+  if (rc) goto done;
+  mat_nn(d, l, d, M, ldm, Q, d, Y, d);                 /* M Q */
+  mat_tn(l, l, d, Q, d, Y, d, B, l);                   /* B = Q^T M Q */
+  for (int j = 0; j < l; ++j)
+    for (int i = j + 1; i < l; ++i) {
+      const double v = 0.5 * (B[(size_t)i + (size_t)j * l] + B[(size_t)j + (size_t)i * l]);
+      B[(size_t)i + (size_t)j * l] = B[(size_t)j + (size_t)i * l] = v;
+    }
+  rc = bko_jacobi_eig(l, B, l, lam, W, l, 100, NULL);
+  if (rc) goto done;
+  mat_nn(d, r, l, Q, d, W, l, U, ldu);                 /* U = Q W[:, :r] */
+  for (int j = 0; j < r; ++j) sigma[j] = lam[j];
+  rc = BKO_OK;
+done:
+  free(Y); free(Q); free(Rt); free(B); free(W); free(lam);
+  return rc;
 }

@@ -28,6 +28,12 @@ MUTANTS = [
     ("linear apply: the step's scale alpha dropped", "srow[j] = alpha * acc;", "srow[j] = acc;"),
     ("relative damping scaled by the smallest eigenvalue", "if (sigma[i] > top) top = sigma[i];",
      "if (sigma[i] < top) top = sigma[i];"),
+    ("EA factor: (1 - rho) dropped from the new term", "const double c = first ? 1.0 / n : (1.0 - rho) / n;",
+     "const double c = first ? 1.0 / n : 1.0 / n;"),
+    ("correction: projects M^2 instead of M", "mat_tn(n_crc, n_crc, d, Us, d, MU, d, Ms, n_crc);",
+     "mat_tn(n_crc, n_crc, d, MU, d, MU, d, Ms, n_crc);"),
+    ("correction: modes not re-sorted", "rc = sort_modes(d, k, U, ldu, sigma);", "rc = BKO_OK;"),
+    ("RSVD: core Q^T Q instead of Q^T M Q", "mat_tn(l, l, d, Q, d, Y, d, B, l);", "mat_tn(l, l, d, Q, d, Q, d, B, l);"),
     ("dense path: rho applied to X X^T instead of U S U^T",
      "K[(size_t)i + (size_t)j * d] = s + c * t;", "K[(size_t)i + (size_t)j * d] = s / rho + rho * c * t;"),
 ]

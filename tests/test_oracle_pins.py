@@ -462,6 +462,111 @@ def test_apply_relative_damping(oracle):
         assert rel(PG, np.linalg.solve(Grep, XG.T).T) < 1e-12
 
 
+# --------------------------------------------------------------------------- dense EA factor, Algorithms 5-6
+
+
+def test_ea_update_is_the_weighted_sum(oracle):
+    """Eq. (5): after batches X_0..X_T the EA factor is sum_j w_j X_j X_j^T / n with
+    w_0 = rho^T (kappa(0) = 1) and w_j = rho^(T-j) (1 - rho); checked as Y Y^T of the
+    weighted concatenation Y = [sqrt(w_j / n) X_j]."""
+    d, n, rho, T = 23, 5, 0.9, 4
+    M = None
+    Ys = []
+    for t in range(T + 1):
+        X = synth.powerlaw_batch(d, n, 1.2, 51, t)
+        M = oracle.ea_update(M, X, rho, first=(t == 0))
+        w = rho ** T if t == 0 else rho ** (T - t) * (1 - rho)
+        Ys.append(np.sqrt(w / n) * X)
+    Y = np.concatenate(Ys, axis=0)
+    assert rel(M, Y.T @ Y) < 1e-13
+
+
+def test_ea_update_matches_untruncated_brand(oracle):
+    """Without truncation the Brand representation is the EA factor itself (Sec. 2.3):
+    two independent pipelines agree."""
+    d, n, rho = 40, 4, 0.95
+    X = synth.powerlaw_batch(d, n, 1.3, 52, 0)
+    M = oracle.ea_update(None, X, rho, first=True)
+    Ut, s, info = oracle.init(X, d)
+    k = info["r_new"]
+    for t in range(1, 5):
+        X = synth.powerlaw_batch(d, n, 1.3, 52, t)
+        M = oracle.ea_update(M, X, rho)
+        Ut, s, info = oracle.update(Ut[:k], s[:k], k, X, rho, d)
+        k = info["r_new"]
+    assert rel(dense(Ut[:k], s[:k]), M) < 1e-12
+
+
+def _truncated_state(oracle, d, r, n, rho, seed, steps):
+    X = synth.powerlaw_batch(d, n, 1.1, seed, 0)
+    M = oracle.ea_update(None, X, rho, first=True)
+    Ut, s, info = oracle.init(X, r)
+    k = info["r_new"]
+    for t in range(1, steps + 1):
+        X = synth.powerlaw_batch(d, n, 1.1, seed, t)
+        M = oracle.ea_update(M, X, rho)
+        Ut, s, info = oracle.update(Ut[:k], s[:k], k, X, rho, r)
+        k = info["r_new"]
+    return Ut[:k], s[:k], M
+
+
+def test_correct_properties(oracle):
+    """Algorithm 6: after the correction the representation agrees with M on the chosen
+    subspace (U_s^T (M - M~) U_s = 0), the Frobenius error does not grow (the paper's
+    footnote), U stays orthonormal, the corrected values are the LAPACK eigenvalues of
+    U_s^T M U_s, and the modes come back sorted."""
+    d, r, n, rho = 60, 12, 6, 0.9
+    Ut, s, M = _truncated_state(oracle, d, r, n, rho, 53, 6)
+    idx = [11, 2, 7, 5, 9, 0]
+    Us = Ut[idx]
+    Uc, sc = oracle.correct(Ut, s, M, idx)
+    assert np.abs(Uc @ Uc.T - np.eye(len(sc))).max() < 1e-12
+    E_new = M - dense(Uc, sc)
+    assert np.linalg.norm(Us @ E_new @ Us.T) < 1e-12 * np.linalg.norm(M)
+    assert np.linalg.norm(E_new) <= np.linalg.norm(M - dense(Ut, s)) * (1 + 1e-12)
+    lam = np.linalg.eigvalsh(Us @ M @ Us.T)
+    for v in lam:
+        assert np.min(np.abs(sc - v)) < 1e-12 * np.abs(lam).max()
+    assert np.all(np.diff(sc) <= 0)
+
+
+def test_correct_is_identity_on_an_exact_representation(oracle):
+    """When M is exactly U diag(sigma) U^T plus a part orthogonal to span(U), the
+    correction changes nothing (up to the order and sign of eigenvectors)."""
+    d, k = 30, 7
+    Ut, s = random_state(d, k, 54)
+    Vt = synth.orthonormal_columns(d, k + 3, 54)[k:]  # orthogonal to span(U)
+    M = dense(Ut, s) + dense(Vt, np.array([0.3, 0.2, 0.1]))
+    Uc, sc = oracle.correct(Ut, s, M, [1, 4, 6])
+    assert rel(dense(Uc, sc), dense(Ut, s)) < 1e-12
+
+
+def test_rsvd_exact_on_low_rank(oracle):
+    """Algorithm 5's RSVD recovers a rank-r0 <= r factor exactly (range finder spans it)."""
+    d, r0, r, l = 50, 6, 8, 12
+    Ut, s = random_state(d, r0, 55)
+    M = dense(Ut, s)
+    Om = np.random.default_rng(56).standard_normal((l, d))
+    U, sig = oracle.rsvd(M, Om, r, q=1)
+    assert rel(dense(U, sig), M) < 1e-12
+    assert np.abs(sig[:r0] - np.sort(s)[::-1]).max() < 1e-12 * s.max()
+
+
+def test_rsvd_gapped_spectrum(oracle):
+    """With a wide gap after r the RSVD's top-r subspace matches LAPACK's."""
+    d, r, l = 64, 5, 10
+    rng = np.random.default_rng(57)
+    Q = synth.orthonormal_columns(d, d, 57)
+    lam = np.concatenate([np.linspace(10, 5, r), 1e-4 * rng.random(d - r)])
+    M = (Q.T * lam) @ Q
+    U, sig = oracle.rsvd(M, rng.standard_normal((l, d)), r, q=3)
+    w, V = np.linalg.eigh(M)
+    Vt = V[:, ::-1][:, :r].T
+    svals = np.linalg.svd(U @ Vt.T, compute_uv=False)
+    assert 1 - svals.min() < 1e-12
+    assert np.abs(sig - w[::-1][:r]).max() < 1e-10
+
+
 # --------------------------------------------------------------------------- planted mistakes
 
 
