@@ -242,6 +242,51 @@ int bkfac_apply_factored(const bkfac_factor* fA, const bkfac_factor* fG, double 
                          int64_t ldpg, double alpha, void* S, int64_t lds, uint32_t flags, void* ws,
                          size_t ws_bytes, bkfac_stream_t stream);
 
+/* ---- B-R-KFAC and B-KFAC-C: the dense EA factor beside the representation --
+ * These variants keep the dense EA K-factor M (d x d) as well, to overwrite
+ * (Algorithm 5) or correct (Algorithm 6) the low-rank representation now and
+ * then.  M is column-major with leading dimension ldm >= d, in the element
+ * type of dtype (double for BKFAC_F64, float otherwise), 16-byte aligned base
+ * and leading dimension.
+ *
+ * Dense EA factor update (Eq. (5) / (8)): M = rho M + (1 - rho)/n X X^T, or
+ * M = X X^T / n when first != 0 (kappa(0) = 1).  X is d x n column-major
+ * (the layout of bkfac_update's X).  In BKFAC_MIXED_BF16 the product takes
+ * BF16-rounded operands with FP32 accumulation.  Work 2 d^2 n flops, traffic
+ * 2 d^2 elements (read and write M). */
+int bkfac_ea_update(int d, int dtype, void* M, int64_t ldm, const void* X, int64_t ldx, int n, double rho,
+                    int first, bkfac_stream_t stream);
+
+/* Light correction of the representation (Algorithm 6, B-KFAC-C): for the
+ * n_crc distinct modes idx[0..n_crc) (0 <= idx < r_cur; a host array, drawn
+ * at random by the caller -- the paper picks them without replacement),
+ *   U_s = U[:, idx],  M_S = U_s^T M U_s = W diag(lam) W^T,
+ *   U[:, idx] = U_s W,  sigma[idx] = lam,
+ * then all r_cur modes are re-sorted by decreasing sigma (stable), so the
+ * representation keeps its order for the next truncation.  M_S is
+ * accumulated in FP64 and factored as M_S = R^T R (FP64 Cholesky) for the
+ * one-sided Jacobi eigensolve.  The copy of idx into the workspace is a
+ * host-to-device copy on `stream`.
+ *   ws  bkfac_correct_workspace_size(f, n_crc) bytes (0: n_crc too large)
+ * Returns BKFAC_EINVAL for repeated or out-of-range indices. */
+size_t bkfac_correct_workspace_size(const bkfac_factor* f, int n_crc);
+int bkfac_correct(bkfac_factor* f, const void* M, int64_t ldm, const int32_t* idx, int n_crc, void* ws,
+                  size_t ws_bytes, bkfac_stream_t stream);
+
+/* RSVD overwrite of the representation (Algorithm 5, B-R-KFAC): a randomised
+ * range finder on M with the caller's test matrix Omega (d x l column-major,
+ * ld ldo, r <= l <= d; the caller draws it, e.g. N(0, 1)) and q power
+ * iterations (q <= 64):
+ *   Y = M Omega;  q times: Q = orth(Y), Y = M Q;  Q = orth(Y);
+ *   B = Q^T M Q = W diag(lam) W^T;  U = Q W[:, :r],  sigma = lam[:r],
+ * with orth by CholeskyQR2 (FP64 Gram and Cholesky) and B by FP64
+ * accumulation, FP64 Cholesky and the one-sided Jacobi eigensolve.  Sets
+ * r_cur = r.
+ *   ws  bkfac_rsvd_workspace_size(f, l) bytes (0: l out of range or too large) */
+size_t bkfac_rsvd_workspace_size(const bkfac_factor* f, int l);
+int bkfac_rsvd(bkfac_factor* f, const void* M, int64_t ldm, const void* Omega, int64_t ldo, int l, int q, void* ws,
+               size_t ws_bytes, bkfac_stream_t stream);
+
 /* The damped inverse application without a caller workspace.  There is no
  * counterpart in the paper: this is an interface for callers that cannot
  * allocate device memory (code running under a stream capture that forbids

@@ -83,6 +83,11 @@ def load(build_if_missing: bool = True):
             "bkfac_apply": ([FP, FP, D, D, P, I64, P, I64, U32, P, S, P], I),
             "bkfac_apply_noalloc": ([FP, FP, D, D, P, I64, P, I64, U32, P], I),
             "bkfac_apply_factored_workspace_size": ([FP, FP, I], S),
+            "bkfac_ea_update": ([I, I, P, I64, P, I64, I, D, I, P], I),
+            "bkfac_correct_workspace_size": ([FP, I], S),
+            "bkfac_correct": ([FP, P, I64, ctypes.POINTER(ctypes.c_int32), I, P, S, P], I),
+            "bkfac_rsvd_workspace_size": ([FP, I], S),
+            "bkfac_rsvd": ([FP, P, I64, P, I64, I, I, P, S, P], I),
             "bkfac_apply_factored": ([FP, FP, D, D, P, I64, P, I64, I, P, I64, P, I64, D, P, I64, U32, P, S, P], I),
             "bkfac_debug_offsets": ([FP, I, ctypes.POINTER(ctypes.c_int64)], I),
             "bkfac_batch_create": ([ctypes.POINTER(bkfac_layer_desc), I, I, I, ctypes.c_char_p], P),
@@ -121,7 +126,8 @@ def exported_symbols():
               "bkfac_debug_offsets", "bkfac_batch_create", "bkfac_batch_get_factor", "bkfac_batch_update",
               "bkfac_batch_apply", "bkfac_batch_step_graph", "bkfac_batch_destroy", "bkfac_trace_enable",
               "bkfac_trace_read", "bkfac_trace_phase_name", "bkfac_apply_noalloc", "bkfac_tune", "bkfac_batch_reorth",
-              "bkfac_apply_factored_workspace_size", "bkfac_apply_factored"):
+              "bkfac_apply_factored_workspace_size", "bkfac_apply_factored", "bkfac_ea_update",
+              "bkfac_correct_workspace_size", "bkfac_correct", "bkfac_rsvd_workspace_size", "bkfac_rsvd"):
         if hasattr(lib, n):
             names.append(n)
     return names
@@ -301,6 +307,48 @@ def bkfac_apply_factored(fA: Factor, fG: Factor, lamA: float, lamG: float, XA: t
         _cols_ld(XG), n, _ptr(PA), _cols_ld(PA), _ptr(PG), _cols_ld(PG), float(alpha),
         _ptr(S) if S is not None else None, S.stride(0) if S is not None else 0, int(flags), _ptr(ws), ws.numel(),
         _stream(stream)), "bkfac_apply_factored")
+
+
+def dense_factor(d: int, dtype: int = F32, device="cuda") -> torch.Tensor:
+    """A zeroed d x d dense EA factor (column-major = a (d, ld) row-major tensor)."""
+    return cols_tensor(d, d, _TORCH_DTYPE[int(dtype)], device)
+
+
+def bkfac_ea_update(M: torch.Tensor, X: torch.Tensor, rho: float, dtype: int, first: bool = False, stream=None):
+    """Dense EA factor M (d x d) <- rho M + (1 - rho)/n X X^T (X: (n, d) columns)."""
+    n, d = X.shape
+    _check(load().bkfac_ea_update(d, int(dtype), _ptr(M), _cols_ld(M), _ptr(X), _cols_ld(X), n, float(rho),
+                                  1 if first else 0, _stream(stream)), "bkfac_ea_update")
+
+
+def bkfac_correct(f: Factor, M: torch.Tensor, idx, ws: torch.Tensor | None = None, stream=None):
+    """Light correction (Algorithm 6) of f along the modes idx against the dense factor M."""
+    ix = (ctypes.c_int32 * len(idx))(*[int(i) for i in idx])
+    if ws is None:
+        key = ("correct", len(idx))
+        if key not in f._ws:
+            nb = load().bkfac_correct_workspace_size(ctypes.byref(f.desc), len(idx))
+            if nb == 0:
+                raise BkfacError(EINVAL, "bkfac_correct_workspace_size")
+            f._ws[key] = workspace(nb, f.U.device)
+        ws = f._ws[key]
+    _check(load().bkfac_correct(ctypes.byref(f.desc), _ptr(M), _cols_ld(M), ix, len(idx), _ptr(ws), ws.numel(),
+                                _stream(stream)), "bkfac_correct")
+
+
+def bkfac_rsvd(f: Factor, M: torch.Tensor, Omega: torch.Tensor, q: int, ws: torch.Tensor | None = None, stream=None):
+    """RSVD overwrite (Algorithm 5) of f from the dense factor M; Omega: (l, d) test columns."""
+    l = Omega.shape[0]
+    if ws is None:
+        key = ("rsvd", l)
+        if key not in f._ws:
+            nb = load().bkfac_rsvd_workspace_size(ctypes.byref(f.desc), l)
+            if nb == 0:
+                raise BkfacError(EINVAL, "bkfac_rsvd_workspace_size")
+            f._ws[key] = workspace(nb, f.U.device)
+        ws = f._ws[key]
+    _check(load().bkfac_rsvd(ctypes.byref(f.desc), _ptr(M), _cols_ld(M), _ptr(Omega), _cols_ld(Omega), l, int(q),
+                             _ptr(ws), ws.numel(), _stream(stream)), "bkfac_rsvd")
 
 
 def bkfac_debug_offsets(f: Factor, n: int):

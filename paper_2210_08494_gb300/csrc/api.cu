@@ -12,6 +12,7 @@
 //   U <- [U Q] V[:, :r_new], sigma <- lambda[:r_new]
 // Dense path (r + n >= d): Jacobi on F = [U sqrt(rho sigma), sqrt(c) X].
 #include <algorithm>
+#include <vector>
 #include <cmath>
 #include <cstring>
 
@@ -594,6 +595,237 @@ int update_common(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho
   return BKFAC_OK;
 }
 
+
+// ------------------------------------------------------------------ B-KFAC-C / B-R-KFAC
+// Small symmetric p.s.d. eigenproblem A = W diag(lam) W^T (A n x n FP64, its lower
+// part read): FP64 Cholesky A = R^T R (pivots below thr_rel * max diag(A) dropped),
+// one-sided Jacobi on L = R^T (L L^T = A), eigenpairs in decreasing order: V (n x n,
+// ld ldv, element type of the factor) and lam (n doubles).
+struct SmallEvd {
+  int n, C, b, rows_pad, cols_pad;
+  int64_t ldv;
+  size_t o_R, o_scale, o_L, o_cn, o_lams, o_V, o_lam, o_sw, o_st;
+};
+
+SmallEvd plan_small_evd(int n, const Prec& pr, Layout& L) {
+  SmallEvd e{};
+  e.n = n;
+  jacobi_plan(std::max(n, 1), std::max(n, 1), pr.jt, &e.C, &e.b, &e.rows_pad, &e.cols_pad);
+  const size_t es = es_of(pr.t), jes = es_of(pr.jt);
+  e.ldv = round_up(std::max(n, 1), 4);
+  e.o_R = L.add((size_t)n * n * 8);
+  e.o_scale = L.add(8);
+  e.o_L = L.add((size_t)e.rows_pad * e.cols_pad * jes);
+  e.o_cn = L.add((size_t)e.cols_pad * 8);
+  e.o_lams = L.add((size_t)e.cols_pad * 8);
+  e.o_V = L.add((size_t)e.ldv * n * es);
+  e.o_lam = L.add((size_t)std::max(n, 1) * 8);
+  e.o_sw = L.add(256);
+  e.o_st = L.add((size_t)e.cols_pad * 4);
+  return e;
+}
+
+bool small_evd_fits(const SmallEvd& e, const Prec& pr) {
+  return e.n >= 1 && jacobi_fits(e.n, e.C, e.b, e.rows_pad, pr.jt) && (size_t)e.n * 12 <= 200 * 1024;
+}
+
+int run_small_evd(const double* A, const SmallEvd& e, const Prec& pr, double thr_rel, void* ws, cudaStream_t s) {
+  double* R = at<double>(ws, e.o_R);
+  double* scale = at<double>(ws, e.o_scale);
+  void* L = at<void>(ws, e.o_L);
+  double* cn = at<double>(ws, e.o_cn);
+  PHASE(PH_CHOL, launch_diag_max(A, e.n, scale, s));
+  PHASE(PH_CHOL, run_chol(A, e.n, R, thr_rel, scale, 0.0, nullptr, s));
+  PHASE(PH_CORE, launch_assemble_transpose(R, e.n, e.rows_pad, e.cols_pad, L, cn, pr.jt, s));
+  JacobiProblem jp;
+  jp.W = L;
+  jp.rows = e.n;
+  jp.cols = e.n;
+  jp.rows_pad = e.rows_pad;
+  jp.cols_pad = e.cols_pad;
+  jp.b = e.b;
+  jp.colnorm2 = cn;
+  jp.sweeps_out = at<int>(ws, e.o_sw);
+  jp.stamp = at<int>(ws, e.o_st);
+  PHASE(PH_JACOBI, launch_jacobi(&jp, 1, e.C, pr.jt, jacobi_tol(e.n, pr.jt), kMaxSweeps, s));
+  SortArgs so;
+  so.W = L;
+  so.rows = e.n;
+  so.rows_pad = e.rows_pad;
+  so.cols = e.n;
+  so.r_out = e.n;
+  so.V = at<void>(ws, e.o_V);
+  so.ldv = e.ldv;
+  so.sig = at<double>(ws, e.o_lam);
+  so.r_sig = e.n;
+  so.lam_sorted = at<double>(ws, e.o_lams);
+  so.colnorm2 = cn;
+  so.cols_pad = e.cols_pad;
+  PHASE(PH_SORT, launch_sort_output(so, pr.jt, pr.t, s));
+  return BKFAC_OK;
+}
+
+// workspace of the light correction (Algorithm 6) along n_crc modes
+struct CorrectPlan {
+  Prec pr;
+  int64_t ldq;
+  SmallEvd e;
+  size_t o_idx, o_Us, o_W, o_Ms, o_part, part_bytes, o_perm, o_sorted, o_Ut, total;
+};
+
+CorrectPlan plan_correct(const bkfac_factor* f, int n_crc) {
+  CorrectPlan p{};
+  p.pr = prec_of(f);
+  p.ldq = ld_of(f->d);
+  const int rt = r_total(f);
+  const size_t es = es_of(p.pr.t);
+  Layout L;
+  p.o_idx = L.add((size_t)std::max(n_crc, 1) * 4);
+  p.o_Us = L.add((size_t)p.ldq * n_crc * es);
+  p.o_W = L.add((size_t)p.ldq * n_crc * es);
+  p.o_Ms = L.add((size_t)n_crc * n_crc * 8);
+  p.part_bytes = std::max((size_t)4 * p.ldq * n_crc * es_of(p.pr.acc), partial_bytes(n_crc, n_crc, f->d, 8));
+  p.o_part = L.add(p.part_bytes);
+  p.o_perm = L.add((size_t)rt * 4);
+  p.o_sorted = L.add((size_t)rt * 8);
+  p.o_Ut = L.add((size_t)p.ldq * rt * es);
+  p.e = plan_small_evd(n_crc, p.pr, L);
+  p.total = L.total;
+  return p;
+}
+
+// W = M B (d x m, M d x d symmetric, B d x m, column-major), factor precision
+int run_dense_times(const void* M, int64_t ldm, int d, const void* B, int64_t ldb, int m, void* W, int64_t ldw,
+                    const Prec& pr, void* part, size_t part_bytes, cudaStream_t s) {
+  GemmArgs g = gemm_base();
+  g.M = d;
+  g.N = m;
+  g.K0 = d;
+  g.A0 = M;
+  g.lda0 = ldm;
+  g.a_kmaj = false;
+  g.B0 = B;
+  g.ldb0 = ldb;
+  g.b_kmaj = true;
+  g.round_bf16 = pr.bf16;
+  g.tf32x3 = pr.x3;
+  g.C = W;
+  g.ldc = ldw;
+  g.partial = part;
+  g.partial_bytes = part_bytes;
+  return gemm_run(g, pr.t, pr.acc, pr.t, s);
+}
+
+// C = A^T B (m x m FP64 output, FP64 accumulation; A, B d x m column-major)
+int run_cross_f64(const void* A, int64_t lda, const void* B, int64_t ldb, int d, int m, double* C, const Prec& pr,
+                  void* part, cudaStream_t s) {
+  GemmArgs g = gemm_base();
+  g.M = m;
+  g.N = m;
+  g.K0 = d;
+  g.A0 = A;
+  g.lda0 = lda;
+  g.a_kmaj = true;
+  g.B0 = B;
+  g.ldb0 = ldb;
+  g.b_kmaj = true;
+  g.C = C;
+  g.ldc = m;
+  g.splits = gemm_pick_splits(m, m, d, 152);
+  g.partial = part;
+  return gemm_run(g, pr.t, DT_F64, DT_F64, s);
+}
+
+// C = A B (d x m; A d x k column-major, B k x m column-major with ld ldb)
+int run_rotate(const void* A, int64_t lda, int d, int k, const void* B, int64_t ldb, int m, void* C, int64_t ldc,
+               const Prec& pr, void* part, size_t part_bytes, cudaStream_t s) {
+  GemmArgs g = gemm_base();
+  g.M = d;
+  g.N = m;
+  g.K0 = k;
+  g.A0 = A;
+  g.lda0 = lda;
+  g.a_kmaj = false;
+  g.B0 = B;
+  g.ldb0 = ldb;
+  g.b_kmaj = true;
+  g.round_bf16 = pr.bf16;
+  g.tf32x3 = pr.x3;
+  g.C = C;
+  g.ldc = ldc;
+  g.partial = part;
+  g.partial_bytes = part_bytes;
+  return gemm_run(g, pr.t, pr.acc, pr.t, s);
+}
+
+// the factor's r_cur modes re-sorted by decreasing sigma (stable)
+int resort_modes(bkfac_factor* f, int* perm, double* sorted, void* Ut, int64_t ldt, const Prec& pr,
+                 cudaStream_t s) {
+  const int k = f->r_cur;
+  PHASE(PH_FINALIZE, launch_mode_order(f->sigma, k, perm, sorted, s));
+  PHASE(PH_FINALIZE, launch_gather_cols(f->U, f->ldu, Ut, ldt, f->d, k, perm, pr.t, s));
+  PHASE(PH_FINALIZE, launch_gather_cols(Ut, ldt, f->U, f->ldu, f->d, k, nullptr, pr.t, s));
+  if (k > 0 && cudaMemcpyAsync(f->sigma, sorted, (size_t)k * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return BKFAC_ECUDA;
+  return BKFAC_OK;
+}
+
+// workspace of the RSVD overwrite (Algorithm 5) with l test columns
+struct RsvdPlan {
+  Prec pr;
+  int64_t ldq;
+  SmallEvd e;
+  size_t o_Y, o_Q1, o_Q, o_G, o_R1, o_R2, o_Rinv, o_flag, o_scale, o_part, part_bytes, total;
+};
+
+RsvdPlan plan_rsvd(const bkfac_factor* f, int l) {
+  RsvdPlan p{};
+  p.pr = prec_of(f);
+  p.ldq = ld_of(f->d);
+  const size_t es = es_of(p.pr.t);
+  Layout L;
+  p.o_Y = L.add((size_t)p.ldq * l * es);
+  p.o_Q1 = L.add((size_t)p.ldq * l * es);
+  p.o_Q = L.add((size_t)p.ldq * l * es);
+  p.o_G = L.add((size_t)l * l * 8);
+  p.o_R1 = L.add((size_t)l * l * 8);
+  p.o_R2 = L.add((size_t)l * l * 8);
+  p.o_Rinv = L.add((size_t)l * l * es);
+  p.o_flag = L.add(16);
+  p.o_scale = L.add(8);
+  p.part_bytes = std::max((size_t)4 * p.ldq * l * es_of(p.pr.acc), partial_bytes(l, l, f->d, 8));
+  p.o_part = L.add(p.part_bytes);
+  p.e = plan_small_evd(l, p.pr, L);
+  p.total = L.total;
+  return p;
+}
+
+// Q = orth(Y) by CholeskyQR2 (FP64 Gram and Cholesky, dropped pivots give zero columns)
+int run_orth(const void* Y, int d, int l, const RsvdPlan& p, void* ws, void* Q, cudaStream_t s) {
+  const Prec& pr = p.pr;
+  void* part = at<void>(ws, p.o_part);
+  double* Gm = at<double>(ws, p.o_G);
+  double* R1 = at<double>(ws, p.o_R1);
+  double* R2 = at<double>(ws, p.o_R2);
+  void* Rinv = at<void>(ws, p.o_Rinv);
+  void* Q1 = at<void>(ws, p.o_Q1);
+  double* scale = at<double>(ws, p.o_scale);
+  int* near = at<int>(ws, p.o_flag);
+  const double ue = pr.bf16 ? 3.90625e-3 : pr.u_t;
+  const double thr1 = (64.0 * ue) * (64.0 * ue);
+  const double thr2 = (64.0 * pr.u_t) * (64.0 * pr.u_t);
+  PHASE(PH_COLNORM, launch_colnorm_max(Y, p.ldq, d, l, pr.t, scale, s));
+  PHASE(PH_GRAM, run_gram(Y, p.ldq, d, l, pr, Gm, part, s));
+  PHASE(PH_CHOL, run_chol(Gm, l, R1, thr1, scale, 0.0, nullptr, s));
+  PHASE(PH_TRINV, launch_trinv(R1, l, Rinv, pr.t, nullptr, s));
+  PHASE(PH_TRMM, run_trmm(Y, p.ldq, d, l, Rinv, pr, Q1, p.ldq, part, p.part_bytes, s));
+  PHASE(PH_GRAM, run_gram(Q1, p.ldq, d, l, pr, Gm, part, s));
+  PHASE(PH_CHOL, run_chol(Gm, l, R2, thr2, nullptr, near_identity_tol(pr), near, s));
+  PHASE(PH_TRINV, launch_trinv(R2, l, Rinv, pr.t, near, s));
+  PHASE(PH_TRMM, run_trmm(Q1, p.ldq, d, l, Rinv, pr, Q, p.ldq, part, p.part_bytes, s));
+  return BKFAC_OK;
+}
+
 }  // namespace
 }  // namespace bkfac
 
@@ -1014,6 +1246,139 @@ int bkfac_apply_factored(const bkfac_factor* fA, const bkfac_factor* fG, double 
     g.alpha = alpha;
     PHASE(PH_FACT_STEP, gemm_run(g, pr.t, pr.acc, pr.t, s));
   }
+  return BKFAC_OK;
+}
+
+int bkfac_ea_update(int d, int dtype, void* M, int64_t ldm, const void* X, int64_t ldx, int n, double rho,
+                    int first, bkfac_stream_t stream) {
+  if (d < 1 || n < 1 || !M || !X || ldm < d || ldx < d) return BKFAC_EINVAL;
+  if (dtype != BKFAC_F64 && dtype != BKFAC_F32 && dtype != BKFAC_MIXED_BF16) return BKFAC_EINVAL;
+  if (!first && !(rho >= 0.0 && rho < 1.0)) return BKFAC_EINVAL;
+  const size_t es = dtype == BKFAC_F64 ? 8 : 4;
+  if (((uintptr_t)M) % 16 != 0 || ((uintptr_t)X) % 16 != 0 || (ldm * (int64_t)es) % 16 != 0 ||
+      (ldx * (int64_t)es) % 16 != 0)
+    return BKFAC_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  bkfac_factor probe{};
+  probe.dtype = dtype;
+  const Prec pr = prec_of(&probe);
+  // M = keep * M + c * X X^T; the epilogue reads M(i, j) before writing it
+  GemmArgs g = gemm_base();
+  g.M = d;
+  g.N = d;
+  g.K0 = n;
+  g.A0 = X;
+  g.lda0 = ldx;
+  g.a_kmaj = false;
+  g.B0 = X;
+  g.ldb0 = ldx;
+  g.b_kmaj = false;
+  g.round_bf16 = pr.bf16;
+  g.tf32x3 = pr.x3;
+  g.C = M;
+  g.ldc = ldm;
+  g.D = first ? nullptr : M;
+  g.ldd = ldm;
+  g.alpha = first ? 1.0 / n : (1.0 - rho) / n;
+  g.beta = first ? 0.0 : rho;
+  PHASE(PH_DENSE, gemm_run(g, pr.t, pr.acc, pr.t, s));
+  return BKFAC_OK;
+}
+
+size_t bkfac_correct_workspace_size(const bkfac_factor* f, int n_crc) {
+  if (!valid_factor(f) || n_crc < 1) return 0;
+  const CorrectPlan p = plan_correct(f, n_crc);
+  if (!small_evd_fits(p.e, p.pr)) return 0;
+  return p.total;
+}
+
+int bkfac_correct(bkfac_factor* f, const void* M, int64_t ldm, const int32_t* idx, int n_crc, void* ws,
+                  size_t ws_bytes, bkfac_stream_t stream) {
+  if (!valid_factor(f) || !M || !idx || n_crc < 1 || n_crc > f->r_cur || ldm < f->d) return BKFAC_EINVAL;
+  const size_t es = f->dtype == BKFAC_F64 ? 8 : 4;
+  if (((uintptr_t)M) % 16 != 0 || (ldm * (int64_t)es) % 16 != 0) return BKFAC_EINVAL;
+  {
+    std::vector<char> seen((size_t)f->r_cur, 0);
+    for (int a = 0; a < n_crc; ++a) {
+      if (idx[a] < 0 || idx[a] >= f->r_cur || seen[(size_t)idx[a]]) return BKFAC_EINVAL;
+      seen[(size_t)idx[a]] = 1;
+    }
+  }
+  const CorrectPlan p = plan_correct(f, n_crc);
+  if (!small_evd_fits(p.e, p.pr)) return BKFAC_EINVAL;
+  int rc = check_ws(ws, ws_bytes, p.total);
+  if (rc) return rc;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const Prec& pr = p.pr;
+  const int d = f->d;
+  int* didx = at<int>(ws, p.o_idx);
+  void* Us = at<void>(ws, p.o_Us);
+  void* W = at<void>(ws, p.o_W);
+  double* Ms = at<double>(ws, p.o_Ms);
+  void* part = at<void>(ws, p.o_part);
+  if (cudaMemcpyAsync(didx, idx, (size_t)n_crc * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return BKFAC_ECUDA;
+  // U_s = U[:, idx];  M_S = U_s^T (M U_s)  (FP64 accumulation)
+  PHASE(PH_PROJ, launch_gather_cols(f->U, f->ldu, Us, p.ldq, d, n_crc, didx, pr.t, s));
+  PHASE(PH_PROJ, run_dense_times(M, ldm, d, Us, p.ldq, n_crc, W, p.ldq, pr, part, p.part_bytes, s));
+  PHASE(PH_GRAM, run_cross_f64(Us, p.ldq, W, p.ldq, d, n_crc, Ms, pr, part, s));
+  // M_S = V diag(lam) V^T;  U[:, idx] = U_s V, sigma[idx] = lam
+  const int erc = run_small_evd(Ms, p.e, pr, (64.0 * pr.u_t) * (64.0 * pr.u_t), ws, s);
+  if (erc) return erc;
+  PHASE(PH_ROTATE, run_rotate(Us, p.ldq, d, n_crc, at<void>(ws, p.e.o_V), p.e.ldv, n_crc, W, p.ldq, pr, part,
+                              p.part_bytes, s));
+  PHASE(PH_FINALIZE, launch_scatter_cols(W, p.ldq, f->U, f->ldu, d, n_crc, didx, at<double>(ws, p.e.o_lam),
+                                         f->sigma, pr.t, s));
+  return resort_modes(f, at<int>(ws, p.o_perm), at<double>(ws, p.o_sorted), at<void>(ws, p.o_Ut), p.ldq, pr, s);
+}
+
+size_t bkfac_rsvd_workspace_size(const bkfac_factor* f, int l) {
+  if (!valid_factor(f) || l < f->r || l > f->d) return 0;
+  const RsvdPlan p = plan_rsvd(f, l);
+  if (!small_evd_fits(p.e, p.pr)) return 0;
+  return p.total;
+}
+
+int bkfac_rsvd(bkfac_factor* f, const void* M, int64_t ldm, const void* Omega, int64_t ldo, int l, int q, void* ws,
+               size_t ws_bytes, bkfac_stream_t stream) {
+  if (!valid_factor(f) || !M || !Omega || ldm < f->d || ldo < f->d || l < f->r || l > f->d || q < 0 || q > 64)
+    return BKFAC_EINVAL;
+  const size_t es = f->dtype == BKFAC_F64 ? 8 : 4;
+  if (((uintptr_t)M) % 16 != 0 || ((uintptr_t)Omega) % 16 != 0 || (ldm * (int64_t)es) % 16 != 0 ||
+      (ldo * (int64_t)es) % 16 != 0)
+    return BKFAC_EINVAL;
+  const RsvdPlan p = plan_rsvd(f, l);
+  if (!small_evd_fits(p.e, p.pr)) return BKFAC_EINVAL;
+  int rc = check_ws(ws, ws_bytes, p.total);
+  if (rc) return rc;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const Prec& pr = p.pr;
+  const int d = f->d, r = f->r;
+  void* Y = at<void>(ws, p.o_Y);
+  void* Q = at<void>(ws, p.o_Q);
+  void* part = at<void>(ws, p.o_part);
+  // Y = M Omega; q power iterations Y = M orth(Y); Q = orth(Y); B = Q^T M Q
+  PHASE(PH_PROJ, run_dense_times(M, ldm, d, Omega, ldo, l, Y, p.ldq, pr, part, p.part_bytes, s));
+  for (int it = 0; it < q; ++it) {
+    rc = run_orth(Y, d, l, p, ws, Q, s);
+    if (rc) return rc;
+    PHASE(PH_PROJ, run_dense_times(M, ldm, d, Q, p.ldq, l, Y, p.ldq, pr, part, p.part_bytes, s));
+  }
+  rc = run_orth(Y, d, l, p, ws, Q, s);
+  if (rc) return rc;
+  PHASE(PH_PROJ, run_dense_times(M, ldm, d, Q, p.ldq, l, Y, p.ldq, pr, part, p.part_bytes, s));
+  double* B = at<double>(ws, p.o_G);
+  PHASE(PH_GRAM, run_cross_f64(Q, p.ldq, Y, p.ldq, d, l, B, pr, part, s));
+  rc = run_small_evd(B, p.e, pr, (64.0 * pr.u_t) * (64.0 * pr.u_t), ws, s);
+  if (rc) return rc;
+  // U = Q V[:, :r], sigma = lam[:r] (the rest of the representation cleared)
+  PHASE(PH_ROTATE, run_rotate(Q, p.ldq, d, l, at<void>(ws, p.e.o_V), p.e.ldv, r, Y, p.ldq, pr, part, p.part_bytes,
+                              s));
+  PHASE(PH_FINALIZE, launch_finalize(f->U, f->ldu, Y, p.ldq, d, r, r_total(f), pr.t, s));
+  if (cudaMemsetAsync(f->sigma, 0, (size_t)r_total(f) * 8, s) != cudaSuccess ||
+      cudaMemcpyAsync(f->sigma, at<double>(ws, p.e.o_lam), (size_t)r * 8, cudaMemcpyDeviceToDevice, s) !=
+          cudaSuccess)
+    return BKFAC_ECUDA;
+  f->r_cur = r;
   return BKFAC_OK;
 }
 

@@ -235,6 +235,21 @@ struct ApplyCoefArgs {
 };
 int launch_apply_coefs(const ApplyCoefArgs& a, cudaStream_t s);
 
+// B-KFAC-C / B-R-KFAC helpers (small.cu)
+// dst[:, j] = src[:, idx[j]] for j < n (idx null: the identity)
+int launch_gather_cols(const void* src, int64_t lds, void* dst, int64_t ldd, int d, int n, const int* idx, DType t,
+                       cudaStream_t s);
+// dst[:, idx[j]] = src[:, j], sig[idx[j]] = lam[j] for j < n
+int launch_scatter_cols(const void* src, int64_t lds, void* dst, int64_t ldd, int d, int n, const int* idx,
+                        const double* lam, double* sig, DType t, cudaStream_t s);
+// *out = max_i G[i, i] of an n x n FP64 matrix
+int launch_diag_max(const double* G, int n, double* out, cudaStream_t s);
+// the Jacobi input L = R^T of an upper n x n FP64 factor (L L^T = R^T R), with column norms
+int launch_assemble_transpose(const double* R, int n, int rows_pad, int cols_pad, void* L, double* colnorm2,
+                              DType j_t, cudaStream_t s);
+// stable order by decreasing value: perm[rank] = i, sorted[rank] = sig[i]
+int launch_mode_order(const double* sig, int k, int* perm, double* sorted, cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // Tracing (trace.cu): per-phase CUDA-event timing and a launch counter
 // ---------------------------------------------------------------------------

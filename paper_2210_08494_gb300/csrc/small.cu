@@ -470,6 +470,77 @@ __global__ void __launch_bounds__(256) apply_coefs_kernel(const ApplyCoefArgs a)
   }
 }
 
+// ---------------------------------------------------------------- B-KFAC-C / B-R-KFAC helpers
+// dst[:, j] = src[:, idx[j]] (idx null: the identity), d rows, grid.y over columns
+template <typename T>
+__global__ void __launch_bounds__(256) gather_cols_kernel(const T* src, int64_t lds, T* dst, int64_t ldd, int d,
+                                                          int n, const int* idx) {
+  for (int j = blockIdx.y; j < n; j += gridDim.y) {
+    const int64_t c = idx ? idx[j] : j;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x)
+      dst[i + (int64_t)j * ldd] = src[i + c * lds];
+  }
+}
+// dst[:, idx[j]] = src[:, j] and sig[idx[j]] = lam[j]
+template <typename T>
+__global__ void __launch_bounds__(256) scatter_cols_kernel(const T* src, int64_t lds, T* dst, int64_t ldd, int d,
+                                                           int n, const int* idx, const double* lam, double* sig) {
+  for (int j = blockIdx.y; j < n; j += gridDim.y) {
+    const int64_t c = idx[j];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x)
+      dst[i + c * ldd] = src[i + (int64_t)j * lds];
+    if (blockIdx.x == 0 && threadIdx.x == 0) sig[c] = lam[j];
+  }
+}
+// out = max_i G[i, i] (n x n, column-major ld n)
+__global__ void __launch_bounds__(256) diag_max_kernel(const double* G, int n, double* out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, G[i + (int64_t)i * n]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+    *out = t;
+  }
+}
+// Jacobi input L = R^T (R n x n upper, column-major ld n: L is lower, L L^T = R^T R),
+// zero padded to rows_pad x cols_pad, with squared column norms; one block per column
+template <typename J>
+__global__ void __launch_bounds__(256) assemble_transpose_kernel(const double* R, int n, int rows_pad, int cols_pad,
+                                                                 J* L, double* colnorm2) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  J* col = L + (int64_t)j * rows_pad;
+  double ss = 0.0;
+  for (int i = threadIdx.x; i < rows_pad; i += blockDim.x) {
+    const J v = (j < n && i < n && i >= j) ? (J)R[j + (int64_t)i * n] : J(0);
+    col[i] = v;
+    ss += (double)v * (double)v;
+  }
+  ss = block_sum(ss, red);
+  if (threadIdx.x == 0) {
+    colnorm2[j] = ss;
+    if (!isfinite(ss)) report(BKFAC_ENONFINITE);
+  }
+}
+// stable order of k modes by decreasing sigma: perm[rank] = i, sorted[rank] = sigma[i]
+__global__ void __launch_bounds__(1024) mode_order_kernel(const double* sig, int k, int* perm, double* sorted) {
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double si = sig[i];
+    if (!isfinite(si)) report(BKFAC_ENONFINITE);
+    int rk = 0;
+    for (int j = 0; j < k; ++j) {
+      const double sj = sig[j];
+      rk += (sj > si) || (sj == si && j < i);
+    }
+    perm[rk] = i;
+    sorted[rk] = si;
+  }
+}
+
 }  // namespace
 
 // ============================================================================ launchers
@@ -606,6 +677,60 @@ int launch_finalize(void* U, int64_t ldu, const void* Unew, int64_t ldn, int d, 
     finalize_kernel<double><<<grid, 256, 0, s>>>((double*)U, ldu, (const double*)Unew, ldn, d, r_new, r);
   else
     finalize_kernel<float><<<grid, 256, 0, s>>>((float*)U, ldu, (const float*)Unew, ldn, d, r_new, r);
+  note_launches(1);
+  return (int)cudaGetLastError();
+}
+
+namespace {
+dim3 col_grid(int d, int n) {
+  return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(d, 256), 16)),
+              (unsigned)std::max(1, std::min(n, 1024)));
+}
+}  // namespace
+
+int launch_gather_cols(const void* src, int64_t lds, void* dst, int64_t ldd, int d, int n, const int* idx, DType t,
+                       cudaStream_t s) {
+  if (n <= 0 || d <= 0) return 0;
+  if (t == DT_F64)
+    gather_cols_kernel<double><<<col_grid(d, n), 256, 0, s>>>((const double*)src, lds, (double*)dst, ldd, d, n, idx);
+  else
+    gather_cols_kernel<float><<<col_grid(d, n), 256, 0, s>>>((const float*)src, lds, (float*)dst, ldd, d, n, idx);
+  note_launches(1);
+  return (int)cudaGetLastError();
+}
+
+int launch_scatter_cols(const void* src, int64_t lds, void* dst, int64_t ldd, int d, int n, const int* idx,
+                        const double* lam, double* sig, DType t, cudaStream_t s) {
+  if (n <= 0 || d <= 0) return 0;
+  if (t == DT_F64)
+    scatter_cols_kernel<double><<<col_grid(d, n), 256, 0, s>>>((const double*)src, lds, (double*)dst, ldd, d, n,
+                                                                idx, lam, sig);
+  else
+    scatter_cols_kernel<float><<<col_grid(d, n), 256, 0, s>>>((const float*)src, lds, (float*)dst, ldd, d, n, idx,
+                                                               lam, sig);
+  note_launches(1);
+  return (int)cudaGetLastError();
+}
+
+int launch_diag_max(const double* G, int n, double* out, cudaStream_t s) {
+  diag_max_kernel<<<1, 256, 0, s>>>(G, n, out);
+  note_launches(1);
+  return (int)cudaGetLastError();
+}
+
+int launch_assemble_transpose(const double* R, int n, int rows_pad, int cols_pad, void* L, double* colnorm2,
+                              DType j_t, cudaStream_t s) {
+  if (j_t == DT_F64)
+    assemble_transpose_kernel<double><<<cols_pad, 256, 0, s>>>(R, n, rows_pad, cols_pad, (double*)L, colnorm2);
+  else
+    assemble_transpose_kernel<float><<<cols_pad, 256, 0, s>>>(R, n, rows_pad, cols_pad, (float*)L, colnorm2);
+  note_launches(1);
+  return (int)cudaGetLastError();
+}
+
+int launch_mode_order(const double* sig, int k, int* perm, double* sorted, cudaStream_t s) {
+  if (k <= 0) return 0;
+  mode_order_kernel<<<1, 1024, 0, s>>>(sig, k, perm, sorted);
   note_launches(1);
   return (int)cudaGetLastError();
 }
