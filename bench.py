@@ -623,6 +623,35 @@ def run_gpu(args, world, rank, local):
                              "gflop": flops / 1e9, "tflops": flops / (ms * 1e-3) / 1e12,
                              "algorithmic_gbytes": nbytes / 1e9, "path": path, "parity_bound": 1e-4}
 
+    # ---- B-KFAC-C / B-R-KFAC pieces on the A factor (d = 4097): the dense EA factor update,
+    # a light correction of 128 modes (phi_crc = 0.5) and an RSVD overwrite (r + 10 test
+    # columns, 4 power iterations)
+    Md = bkfac.dense_factor(D_A, bkfac.F32, dev)
+    bkfac.bkfac_ea_update(Md, XA[0], RHO, bkfac.F32, first=True)
+    gB = bkfac.Factor(D_A, R, bkfac.F32, device=dev)
+    bkfac.bkfac_init(gB, XA[0])
+    idx_crc = [int(i) for i in np.random.default_rng(seedA + 7).choice(R, R // 2, replace=False)]
+    Om = bkfac.cols_tensor(R + 10, D_A, torch.float32, dev)
+    Om.normal_(generator=torch.Generator(device=dev).manual_seed(seedA + 8))
+    ea_fn = lambda t: bkfac.bkfac_ea_update(Md, XA[xi(t)], RHO, bkfac.F32)  # noqa: E731
+    crc_fn = lambda t: bkfac.bkfac_correct(gB, Md, idx_crc)  # noqa: E731
+    rsvd_fn = lambda t: bkfac.bkfac_rsvd(gB, Md, Om, 4)  # noqa: E731
+    for fn in (ea_fn, crc_fn, rsvd_fn):
+        for t in range(2):
+            fn(t)
+    l_rs = R + 10
+    variants_dense = {}
+    for name, fn, flops, nbytes, path in (
+            ("ea_update", ea_fn, 2.0 * D_A * D_A * N, 2.0 * D_A * D_A * 4,
+             "dense EA factor M = rho M + (1 - rho)/n X X^T (d = 4097, n = 256, FP32)"),
+            ("correct_alg6", crc_fn, 2.0 * D_A * D_A * (R // 2), D_A * D_A * 4.0,
+             "light correction of 128 of 256 modes against M (Algorithm 6)"),
+            ("rsvd_alg5", rsvd_fn, 2.0 * D_A * D_A * l_rs * 6, 6.0 * D_A * D_A * 4,
+             "RSVD overwrite, l = 266 test columns, 4 power iterations (Algorithm 5)")):
+        ms = time_calls(fn, max(min(args.steps, 5), 3))
+        variants_dense[name] = {"ms": ms, "gflop": flops / 1e9, "tflops": flops / (ms * 1e-3) / 1e12,
+                                "algorithmic_gbytes": nbytes / 1e9, "path": path, "parity_bound": 1e-4}
+
     batched = {} if args.no_batched else {
         "f32_graph": run_batched(args, bkfac, synth, torch, dev, seedA, seedG, bkfac.F32, flush),
         "mixed_bf16_graph": run_batched(args, bkfac, synth, torch, dev, seedA, seedG, bkfac.MIXED_BF16, flush),
@@ -650,6 +679,7 @@ def run_gpu(args, world, rank, local):
             "batched": batched,
             "variants": variants,
             "apply": apply_lines,
+            "dense_factor_variants": variants_dense,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

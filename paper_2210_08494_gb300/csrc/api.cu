@@ -1262,7 +1262,9 @@ int bkfac_ea_update(int d, int dtype, void* M, int64_t ldm, const void* X, int64
   bkfac_factor probe{};
   probe.dtype = dtype;
   const Prec pr = prec_of(&probe);
-  // M = keep * M + c * X X^T; the epilogue reads M(i, j) before writing it
+  // M = keep * M + c * X X^T; the epilogue reads M(i, j) before writing it.  M is
+  // symmetric, so it is written (and read) as its row-major transpose: whole rows
+  // of the output tile go out coalesced
   GemmArgs g = gemm_base();
   g.M = d;
   g.N = d;
@@ -1277,6 +1279,7 @@ int bkfac_ea_update(int d, int dtype, void* M, int64_t ldm, const void* X, int64
   g.tf32x3 = pr.x3;
   g.C = M;
   g.ldc = ldm;
+  g.c_rowmaj = true;
   g.D = first ? nullptr : M;
   g.ldd = ldm;
   g.alpha = first ? 1.0 / n : (1.0 - rho) / n;
