@@ -297,6 +297,8 @@ P* at(void* ws, size_t off) {
 // near_out (may be null) receives whether the near-identity shortcut was taken
 int run_chol(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
              int* near_out, cudaStream_t s) {
+  // the blocked 2D block-cyclic kernel spreads every step over the cluster
+  if (chol_block_ok(n)) return launch_chol_block(Gm, n, R, thr_rel, scale, near_tol, near_out, s);
   if (chol_cluster_size(n) > 0) return launch_chol_cluster(Gm, n, R, thr_rel, scale, near_tol, near_out, s);
   if (near_out != nullptr && cudaMemsetAsync(near_out, 0, sizeof(int), s) != cudaSuccess) return BKFAC_ECUDA;
   return launch_chol(Gm, n, R, thr_rel, scale, s);

@@ -169,7 +169,243 @@ __global__ void __launch_bounds__(CT) chol_cluster_kernel(const double* __restri
   cluster.sync();  // keep shared memory alive until every remote read is done
 }
 
+// ---------------------------------------------------------------------------
+// Blocked right-looking Cholesky on a 4 x 4 grid of CTAs (a 16-CTA cluster),
+// for the first CholeskyQR pass.  The lower triangle is cut into 16 x 16
+// blocks; block (i, j) lives in CTA (i mod 4, j mod 4) (2D block-cyclic), so
+// that every step spreads its work over the cluster.  Step k:
+//   A  the owner of (k, k) factors it with one warp (lane = row, pivots
+//      broadcast by shuffles; a pivot <= thr is dropped: its column of L is
+//      zero) and keeps the reciprocals of the diagonal;
+//   B  the owners of the blocks (i, k), i > k, solve L_ik L_kk^T = A_ik row by
+//      row, with L_kk read from the diagonal owner's shared memory;
+//   C  every CTA updates its trailing blocks, A_ij -= L_ik L_jk^T, with the
+//      panel blocks it needs copied from their owners.
+// Two cluster barriers per step (after A, after B); C needs none: its inputs
+// are never written again, and the next diagonal block is updated by its own
+// owner.  FP64 throughout.  Blocks are row-major in shared memory.
+// With near_tol > 0 the kernel first applies the near-identity test of the
+// second CholeskyQR pass to its blocks (all CTAs take the cluster's decision)
+// and, when it holds, writes R = I + Phi(E) instead of factoring.
+constexpr int CB = 16;     // block size
+constexpr int CBT = 512;   // threads per CTA
+
+__device__ __forceinline__ int blk_rank(int pr, int pc) { return pr * 4 + pc; }
+
+__global__ void __launch_bounds__(CBT) chol_block_kernel(const double* __restrict__ Gm, int n, double* R,
+                                                         double thr_rel, const double* scale, double near_tol,
+                                                         int* near_out) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int pr = rank / 4, pc = rank % 4;
+  const int nb = (n + CB - 1) / CB, S = (nb + 3) / 4;
+  extern __shared__ __align__(16) double bsm[];
+  double* slots = bsm;                       // S x S blocks: block (4a + pr, 4b + pc) at slot a * S + b
+  double* Li = slots + (size_t)S * S * 256;  // S cached panel blocks (rows of this CTA)
+  double* Lj = Li + (size_t)S * 256;         // S cached panel blocks (columns of this CTA)
+  double* Lkk = Lj + (size_t)S * 256;        // the current diagonal block
+  double* inv = Lkk + 256;                   // its reciprocal diagonal (0 for dropped pivots)
+  double* inv_local = inv + 16;
+  auto slot = [&](int a, int b) { return slots + (size_t)(a * S + b) * 256; };
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const double thr = thr_rel * (scale ? *scale : 1.0);
+
+  // load the owned lower blocks (entries past n are zero: their pivots are dropped)
+  for (int e = tid; e < S * S * 256; e += CBT) {
+    const int sl = e >> 8, w = e & 255, a = sl / S, b = sl % S;
+    const int i = 4 * a + pr, j = 4 * b + pc;
+    const int row = CB * i + (w >> 4), col = CB * j + (w & 15);
+    slots[e] = (i < nb && j <= i && row < n && col < n && row >= col) ? Gm[row + (int64_t)col * n] : 0.0;
+  }
+  __shared__ int s_flag[2];  // [0]: this CTA's blocks are near identity, [1]: the cluster's decision
+  if (tid == 0) s_flag[0] = 1;
+  __syncthreads();
+  if (near_tol > 0.0) {
+    // integer compares of the IEEE bit patterns (|g| <= tol off the diagonal,
+    // 1 - tol <= g <= 1 + tol on it; NaN fails): no FP64 arithmetic
+    const long long tolb = __double_as_longlong(near_tol);
+    const long long lob = __double_as_longlong(1.0 - near_tol), hib = __double_as_longlong(1.0 + near_tol);
+    bool ok = true;
+    for (int e = tid; e < S * S * 256; e += CBT) {
+      const int sl = e >> 8, w = e & 255, a = sl / S, b = sl % S;
+      const int i = 4 * a + pr, j = 4 * b + pc;
+      const int row = CB * i + (w >> 4), col = CB * j + (w & 15);
+      if (i >= nb || j > i || row >= n || col >= n || row < col) continue;
+      const long long bits = __double_as_longlong(slots[e]);
+      ok = ok && (row == col ? (bits >= lob && bits <= hib) : (bits & 0x7fffffffffffffffLL) <= tolb);
+    }
+    if (!ok) s_flag[0] = 0;  // benign race: every writer stores 0
+  } else if (tid == 0) {
+    s_flag[0] = 0;
+  }
+  cluster.sync();
+  if (tid == 0) {
+    int all = 1;
+    for (int q = 0; q < 16; ++q) all &= *cluster.map_shared_rank(&s_flag[0], q);
+    s_flag[1] = all;
+  }
+  __syncthreads();
+  const bool near = s_flag[1] != 0;
+  if (near_out != nullptr && rank == 0 && tid == 0) *near_out = near ? 1 : 0;
+
+  for (int k = 0; k < (near ? 0 : nb); ++k) {
+    const int dk = k & 3, kb = k >> 2;
+    // ---- A: factor the diagonal block, all warps of its owner: per column one
+    // thread takes the pivot, then the column's scaling and the rank-1 update of
+    // the block's trailing lower entries run in parallel (one FP64 operation each),
+    // the update written with the unscaled column and 1/pivot:
+    //   D[r][c] -= D[r][j] D[c][j] / p,   L[r][j] = D[r][j] / sqrt(p)
+    if (pr == dk && pc == dk) {
+      double* D = slot(kb, kb);
+      __shared__ double s_piv[2];  // 1/sqrt(p), 1/p (0 for a dropped pivot)
+      for (int j = 0; j < CB; ++j) {
+        if (tid == 0) {
+          const double piv = D[j * CB + j];
+          const bool keep = piv > thr;  // false for NaN as well
+          if (!isfinite(piv)) report(BKFAC_ENONFINITE);
+          double l = 0.0, il = 0.0;
+          if (keep) {
+            if (piv > 1e-30 && piv < 1e30) {
+              // 1/sqrt(piv): the FP32 hardware approximation (about 2^-22 relative
+              // error) refined by one Newton step for x^(-1/2),
+              // y <- y + y (1 - x y^2) / 2, which squares the error (about 4e-14);
+              // FP64 square root and division are long sequences on this GPU's
+              // FP64 pipe, and this chain runs once per column
+              double y = (double)rsqrtf((float)piv);
+              const double e = fma(-piv * y, y, 1.0);
+              y = fma(0.5 * y, e, y);
+              l = piv * y;
+              il = y;
+            } else {
+              l = sqrt(piv);
+              il = 1.0 / l;
+            }
+          }
+          D[j * CB + j] = l;
+          inv[j] = il;
+          s_piv[0] = il;
+          s_piv[1] = il * il;
+        }
+        __syncthreads();
+        const double il = s_piv[0], ip = s_piv[1];
+        // trailing entries (r, c), j < c <= r < 16 (at most 120), and the column scaling
+        for (int t = tid; t < CB * CB; t += CBT) {
+          const int r = t >> 4, c = t & 15;
+          if (c > j && c <= r) D[r * CB + c] -= D[r * CB + j] * D[c * CB + j] * ip;
+        }
+        __syncthreads();
+        if (tid > j && tid < CB) D[tid * CB + j] *= il;
+        if (tid < j) D[tid * CB + j] = 0.0;  // the strict upper part stays zero
+        __syncthreads();
+      }
+    }
+    cluster.sync();  // L_kk and its reciprocals are final
+    // ---- B: the panel blocks below the diagonal, owned by the CTAs of grid column dk
+    if (pc == dk) {
+      const int src = blk_rank(dk, dk);
+      const double* rL = cluster.map_shared_rank(slot(kb, kb), src);
+      const double* rI = cluster.map_shared_rank(inv, src);
+      for (int e = tid; e < 256; e += CBT) Lkk[e] = rL[e];
+      if (tid < 16) inv_local[tid] = rI[tid];
+      __syncthreads();
+      // one thread per row of each owned block (i, k), i > k
+      for (int t = tid; t < S * CB; t += CBT) {
+        const int a = t / CB, r = t % CB, i = 4 * a + pr;
+        if (i <= k || i >= nb) continue;
+        double* B = slot(a, kb) + r * CB;
+        double x[CB];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) x[c] = B[c];
+#pragma unroll
+        for (int j = 0; j < CB; ++j) {
+          double v = x[j];
+#pragma unroll
+          for (int m = 0; m < j; ++m) v -= x[m] * Lkk[j * CB + m];
+          x[j] = v * inv_local[j];
+        }
+#pragma unroll
+        for (int c = 0; c < CB; ++c) B[c] = x[c];
+      }
+    }
+    cluster.sync();  // the panel of step k is final
+    // ---- C: trailing update of the owned blocks (i, j), k < j <= i
+    {
+      const int rsrc = blk_rank(pr, dk), csrc = blk_rank(pc, dk);
+      for (int e = tid; e < 2 * S * 256; e += CBT) {
+        const int half = e / (S * 256), w = e % (S * 256), a = w >> 8, o = w & 255;
+        const int g = 4 * a + (half ? pc : pr);
+        if (g <= k || g >= nb) continue;
+        const double* src = cluster.map_shared_rank(slot(a, kb), half ? csrc : rsrc);
+        (half ? Lj : Li)[w] = src[o];
+      }
+      __syncthreads();
+      for (int e = tid; e < S * S * 256; e += CBT) {
+        const int sl = e >> 8, w = e & 255, a = sl / S, b = sl % S;
+        const int i = 4 * a + pr, j = 4 * b + pc;
+        if (j <= k || j > i || i >= nb) continue;
+        const int r = w >> 4, c = w & 15;
+        const double* li = Li + a * 256 + r * CB;
+        const double* lj = Lj + b * 256 + c * CB;
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < CB; ++m) acc += li[m] * lj[m];
+        slots[e] -= acc;
+      }
+      __syncthreads();
+    }
+  }
+  // R = L^T (upper), or I + Phi(E) when near identity (E = G - I: its strict upper
+  // part plus half its diagonal); the strictly lower part of R is zero
+  for (int e = tid; e < S * S * 256; e += CBT) {
+    const int sl = e >> 8, w = e & 255, a = sl / S, b = sl % S;
+    const int i = 4 * a + pr, j = 4 * b + pc;
+    if (i >= nb || j > i) continue;
+    const int row = CB * i + (w >> 4), col = CB * j + (w & 15);
+    if (row >= n || col >= n) continue;
+    const double v = slots[e];
+    R[col + (int64_t)row * n] = row < col ? 0.0 : (!near ? v : (row == col ? 1.0 + 0.5 * (v - 1.0) : v));
+    if (row > col) R[row + (int64_t)col * n] = 0.0;
+  }
+  cluster.sync();  // keep shared memory alive until every remote read is done
+}
+
 }  // namespace
+
+// blocked cluster Cholesky: n x n with n <= 576 (at most 9 x 9 blocks per CTA)
+size_t chol_block_smem(int n) {
+  const int nb = (n + CB - 1) / CB, S = (nb + 3) / 4;
+  return ((size_t)S * S + 2 * (size_t)S + 1) * 256 * sizeof(double) + 32 * sizeof(double);
+}
+
+bool chol_block_ok(int n) { return n >= 32 && chol_block_smem(n) <= 200 * 1024; }
+
+int launch_chol_block(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
+                      int* near_out, cudaStream_t s) {
+  if (!chol_block_ok(n)) return (int)cudaErrorInvalidValue;
+  static std::atomic<int> configured{0};
+  if (!configured.load()) {
+    cudaError_t e = cudaFuncSetAttribute(chol_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(chol_block_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return (int)e;
+    configured.store(1);
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(16, 1, 1);
+  cfg.blockDim = dim3(CBT, 1, 1);
+  cfg.dynamicSmemBytes = chol_block_smem(n);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 16;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, chol_block_kernel, Gm, n, R, thr_rel, scale, near_tol, near_out);
+  note_launches(1);
+  return (int)e;
+}
 
 // cluster size for an n x n factorisation (two n x w FP64 buffers per CTA)
 int chol_cluster_size(int n) {

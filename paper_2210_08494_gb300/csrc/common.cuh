@@ -121,6 +121,11 @@ int launch_chol(const double* Gm, int n, double* R, double thr_rel, const double
 int launch_chol_cluster(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
                         int* near_out, cudaStream_t s);
 int chol_cluster_size(int n);  // 0 when n is too large for the cluster kernel
+// blocked (2D block-cyclic, 16 x 16 blocks) FP64 Cholesky on a 16-CTA cluster with the
+// near-identity shortcut of the second CholeskyQR pass (near_tol > 0); for 32 <= n <= 576
+bool chol_block_ok(int n);
+int launch_chol_block(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
+                      int* near_out, cudaStream_t s);
 // inverse of the upper-triangular R (zero rows = dropped pivots -> zero rows/cols of Rinv);
 // when near (may be null) points to a nonzero flag, R = I + F is near identity and
 // Rinv = I - F (exact to O(|F|^2)) is written instead
