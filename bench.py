@@ -185,9 +185,9 @@ def cpu_baseline_sample():
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
-# kernel on this workload (the 512-column update eigensolve: 1.134 MB read, 0 written;
+# kernel on this workload (the 512-column update eigensolve: 1.136 MB read, 0 written;
 # the blocks live in shared memory and registers).  Reset to None when the kernel changes.
-DRAM_BYTES_PER_LAUNCH = {"jacobi": 1134336}
+DRAM_BYTES_PER_LAUNCH = {"jacobi": 1136128}
 
 
 def algorithmic_work(phase, ms, counts, sweeps):
@@ -604,14 +604,14 @@ def run_gpu(args, world, rank, local):
     fact_apply = lambda t: bkfac.bkfac_apply_factored(fA, fG, LAM, LAM, XA[xi(t)], XG[xi(t)], PA, PG,  # noqa: E731
                                                       alpha=1.0 / N, S=S)
     thin_apply = lambda t: bkfac.bkfac_apply_factored(fA, fG, LAM, LAM, XA[xi(t)], XG[xi(t)], PA, PG)  # noqa: E731
-    for fn in (dense_apply, fact_apply, thin_apply):
+    for fn in ((dense_apply, fact_apply, thin_apply) if not args.no_batched else ()):
         for t in range(args.warmup):
             fn(t)
     flops_dense = 4.0 * D_G * D_A * (R + R)
     flops_thin = 4.0 * N * (R * D_A + R * D_G)
     flops_fact = flops_thin + 2.0 * D_G * D_A * N
     apply_lines = {}
-    for name, fn, flops, nbytes, path in (
+    for name, fn, flops, nbytes, path in () if args.no_batched else (
             ("dense_alg1", dense_apply, flops_dense, 2 * D_G * D_A * 4,
              "Algorithm 1 on the dense 4096 x 4097 gradient (two passes over G)"),
             ("factored_alg8", fact_apply, flops_fact, (N * (2 * D_A + 2 * D_G) + D_G * D_A) * 4,
@@ -626,31 +626,10 @@ def run_gpu(args, world, rank, local):
     # ---- B-KFAC-C / B-R-KFAC pieces on the A factor (d = 4097): the dense EA factor update,
     # a light correction of 128 modes (phi_crc = 0.5) and an RSVD overwrite (r + 10 test
     # columns, 4 power iterations)
-    Md = bkfac.dense_factor(D_A, bkfac.F32, dev)
-    bkfac.bkfac_ea_update(Md, XA[0], RHO, bkfac.F32, first=True)
-    gB = bkfac.Factor(D_A, R, bkfac.F32, device=dev)
-    bkfac.bkfac_init(gB, XA[0])
-    idx_crc = [int(i) for i in np.random.default_rng(seedA + 7).choice(R, R // 2, replace=False)]
-    Om = bkfac.cols_tensor(R + 10, D_A, torch.float32, dev)
-    Om.normal_(generator=torch.Generator(device=dev).manual_seed(seedA + 8))
-    ea_fn = lambda t: bkfac.bkfac_ea_update(Md, XA[xi(t)], RHO, bkfac.F32)  # noqa: E731
-    crc_fn = lambda t: bkfac.bkfac_correct(gB, Md, idx_crc)  # noqa: E731
-    rsvd_fn = lambda t: bkfac.bkfac_rsvd(gB, Md, Om, 4)  # noqa: E731
-    for fn in (ea_fn, crc_fn, rsvd_fn):
-        for t in range(2):
-            fn(t)
-    l_rs = R + 10
     variants_dense = {}
-    for name, fn, flops, nbytes, path in (
-            ("ea_update", ea_fn, 2.0 * D_A * D_A * N, 2.0 * D_A * D_A * 4,
-             "dense EA factor M = rho M + (1 - rho)/n X X^T (d = 4097, n = 256, FP32)"),
-            ("correct_alg6", crc_fn, 2.0 * D_A * D_A * (R // 2), D_A * D_A * 4.0,
-             "light correction of 128 of 256 modes against M (Algorithm 6)"),
-            ("rsvd_alg5", rsvd_fn, 2.0 * D_A * D_A * l_rs * 6, 6.0 * D_A * D_A * 4,
-             "RSVD overwrite, l = 266 test columns, 4 power iterations (Algorithm 5)")):
-        ms = time_calls(fn, max(min(args.steps, 5), 3))
-        variants_dense[name] = {"ms": ms, "gflop": flops / 1e9, "tflops": flops / (ms * 1e-3) / 1e12,
-                                "algorithmic_gbytes": nbytes / 1e9, "path": path, "parity_bound": 1e-4}
+    if not args.no_batched:
+        variants_dense = dense_factor_variants(args, bkfac, torch, np, dev, XA, xi, time_calls, seedA)
+
 
     batched = {} if args.no_batched else {
         "f32_graph": run_batched(args, bkfac, synth, torch, dev, seedA, seedG, bkfac.F32, flush),
@@ -685,6 +664,38 @@ def run_gpu(args, world, rank, local):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def dense_factor_variants(args, bkfac, torch, np, dev, XA, xi, time_calls, seedA):
+    """B-KFAC-C / B-R-KFAC pieces on the wide layer's A factor (d = 4097): the dense EA factor
+    update, a light correction of 128 modes (phi_crc = 0.5) and an RSVD overwrite (r + 10 test
+    columns, 4 power iterations)."""
+    out = {}
+    Md = bkfac.dense_factor(D_A, bkfac.F32, dev)
+    bkfac.bkfac_ea_update(Md, XA[0], RHO, bkfac.F32, first=True)
+    gB = bkfac.Factor(D_A, R, bkfac.F32, device=dev)
+    bkfac.bkfac_init(gB, XA[0])
+    idx_crc = [int(i) for i in np.random.default_rng(seedA + 7).choice(R, R // 2, replace=False)]
+    Om = bkfac.cols_tensor(R + 10, D_A, torch.float32, dev)
+    Om.normal_(generator=torch.Generator(device=dev).manual_seed(seedA + 8))
+    ea_fn = lambda t: bkfac.bkfac_ea_update(Md, XA[xi(t)], RHO, bkfac.F32)  # noqa: E731
+    crc_fn = lambda t: bkfac.bkfac_correct(gB, Md, idx_crc)  # noqa: E731
+    rsvd_fn = lambda t: bkfac.bkfac_rsvd(gB, Md, Om, 4)  # noqa: E731
+    for fn in (ea_fn, crc_fn, rsvd_fn):
+        for t in range(2):
+            fn(t)
+    l_rs = R + 10
+    for name, fn, flops, nbytes, path in (
+            ("ea_update", ea_fn, 2.0 * D_A * D_A * N, 2.0 * D_A * D_A * 4,
+             "dense EA factor M = rho M + (1 - rho)/n X X^T (d = 4097, n = 256, FP32)"),
+            ("correct_alg6", crc_fn, 2.0 * D_A * D_A * (R // 2), D_A * D_A * 4.0,
+             "light correction of 128 of 256 modes against M (Algorithm 6)"),
+            ("rsvd_alg5", rsvd_fn, 2.0 * D_A * D_A * l_rs * 6, 6.0 * D_A * D_A * 4,
+             "RSVD overwrite, l = 266 test columns, 4 power iterations (Algorithm 5)")):
+        ms = time_calls(fn, max(min(args.steps, 5), 3))
+        out[name] = {"ms": ms, "gflop": flops / 1e9, "tflops": flops / (ms * 1e-3) / 1e12,
+                     "algorithmic_gbytes": nbytes / 1e9, "path": path, "parity_bound": 1e-4}
+    return out
 
 
 def main():
