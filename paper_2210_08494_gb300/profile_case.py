@@ -23,8 +23,8 @@ from . import bkfac, synth
 DTYPES = {"f32": bkfac.F32, "f64": bkfac.F64, "mixed": bkfac.MIXED_BF16}
 
 
-def factor_with_updates(d, r, n, dtype, updates, seed, alpha):
-    f = bkfac.Factor(d, r, dtype)
+def factor_with_updates(d, r, n, dtype, updates, seed, alpha, flags=0):
+    f = bkfac.Factor(d, r, dtype, flags=flags)
     tdt = torch.float64 if dtype == bkfac.F64 else torch.float32
     xs = []
     for t in range(updates + 1):
@@ -37,11 +37,11 @@ def factor_with_updates(d, r, n, dtype, updates, seed, alpha):
     return f
 
 
-def factor_with_state(d, r, dtype, seed):
+def factor_with_state(d, r, dtype, seed, flags=0):
     """A factor holding r orthonormal columns and a power-law spectrum (no updates)."""
     import numpy as np
 
-    f = bkfac.Factor(d, r, dtype)
+    f = bkfac.Factor(d, r, dtype, flags=flags)
     Ut = synth.orthonormal_columns(d, r, seed)
     sig = np.arange(1, r + 1, dtype=np.float64) ** -1.2
     f.load_state(torch.from_numpy(Ut).to(f.torch_dtype).cuda(), torch.from_numpy(sig).cuda())
@@ -60,22 +60,24 @@ def main(argv=None):
     ap.add_argument("--synthetic-state", action="store_true",
                     help="with --apply: load orthonormal factor states instead of running updates")
     ap.add_argument("--repeat", type=int, default=1, help="with --apply: time this many applications")
+    ap.add_argument("--tf32x3", action="store_true", help="FP32 products as 3xTF32 on the tensor cores")
     args = ap.parse_args(argv)
     bkfac.load()
     bkfac.bkfac_status()
     dtype = DTYPES[args.dtype]
+    fl = bkfac.FLAG_TF32X3 if args.tf32x3 else 0
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record()
     if args.synthetic_state:
-        fA = factor_with_state(args.d, args.r, dtype, 2000)
+        fA = factor_with_state(args.d, args.r, dtype, 2000, fl)
     else:
-        fA = factor_with_updates(args.d, args.r, args.n, dtype, args.updates, 2000, args.alpha)
+        fA = factor_with_updates(args.d, args.r, args.n, dtype, args.updates, 2000, args.alpha, fl)
     end.record()
     if args.apply:
         if args.synthetic_state:
-            fG = factor_with_state(args.apply, args.r, dtype, 2001)
+            fG = factor_with_state(args.apply, args.r, dtype, 2001, fl)
         else:
-            fG = factor_with_updates(args.apply, args.r, args.n, dtype, args.updates, 2001, args.alpha)
+            fG = factor_with_updates(args.apply, args.r, args.n, dtype, args.updates, 2001, args.alpha, fl)
         tdt = torch.float64 if dtype == bkfac.F64 else torch.float32
         G = bkfac.grad_tensor(args.apply, args.d, tdt)
         G.normal_(generator=torch.Generator(device="cuda").manual_seed(7))
