@@ -355,8 +355,23 @@ __device__ __forceinline__ float4 ld_b4(const GemmArgs& g, int k, int n, int ke,
   return v;
 }
 
+// two-wide FP32 FMA (fma.rn.f32x2): d = a * b + c on packed pairs
+__device__ __forceinline__ uint64_t ffma2_g(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t pack2_g(float lo, float hi) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void unpack2_g(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
 template <bool AK, bool BKM>
-__global__ void __launch_bounds__(LNT) sgemm_large_kernel(const GemmArgs g) {
+__global__ void __launch_bounds__(LNT, 2) sgemm_large_kernel(const GemmArgs g) {
   __shared__ __align__(16) float As[2][LBK][LBM];
   __shared__ __align__(16) float Bs[2][LBK][LBN];
   const int tid = threadIdx.x;
@@ -372,11 +387,21 @@ __global__ void __launch_bounds__(LNT) sgemm_large_kernel(const GemmArgs g) {
   const int bn = BKM ? (tid >> 1) : ((tid & 31) << 2);
   const int bk = BKM ? ((tid & 1) << 2) : (tid >> 5);
 
+  // With both operands M/N-contiguous (16-byte tile loads, global loads well ahead of use)
+  // the accumulators are packed pairs along n, acc2[i][p] = columns 2p, 2p + 1 of row i, and
+  // the inner product runs on the two-wide FMA: half the issue slots of scalar FMAs.  With a
+  // K-contiguous operand the shorter loop no longer hides the next tile's global loads
+  // (measured slower), so those layouts keep scalar FMAs.
+  constexpr bool kPair = !AK && !BKM;
+  uint64_t acc2[8][4];
   float acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int p = 0; p < 4; ++p) {
+      acc2[i][p] = 0ull;  // (0.f, 0.f)
+      acc[i][2 * p] = acc[i][2 * p + 1] = 0.f;
+    }
 
   auto store_tile = [&](int buf, const float4& va, const float4& vb) {
     if (AK) {
@@ -418,17 +443,34 @@ __global__ void __launch_bounds__(LNT) sgemm_large_kernel(const GemmArgs g) {
       const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
       const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
       const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      if constexpr (kPair) {
+        const uint64_t b2[4] = {pack2_g(b0.x, b0.y), pack2_g(b0.z, b0.w), pack2_g(b1.x, b1.y),
+                                pack2_g(b1.z, b1.w)};
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i) {
+          const uint64_t ai = pack2_g(a[i], a[i]);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+          for (int p = 0; p < 4; ++p) acc2[i][p] = ffma2_g(ai, b2[p], acc2[i][p]);
+        }
+      } else {
+        const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
     }
     if (more) store_tile(buf ^ 1, na, nb);
     __syncthreads();
     buf ^= 1;
   }
 
+  if constexpr (kPair) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) unpack2_g(acc2[i][p], acc[i][2 * p], acc[i][2 * p + 1]);
+  }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
