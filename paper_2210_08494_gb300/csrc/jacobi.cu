@@ -344,11 +344,13 @@ __device__ __forceinline__ unsigned y_mask(unsigned rot) {
 // Each column thus crosses shared memory once per K pairs instead of once per
 // pair, and each step has K independent reduction chains in flight.  s_nrm /
 // s_stamp hold the squared norms and the sweep of each column's last rotation
-// (stamps of block I at s_stamp[0, b), of block J at s_stamp[32, 32 + b)).
+// (block I at [0, b), block J at [32, 32 + b)).  The norms are recomputed from
+// the columns when `refresh` is set (resetting the drift of the tracked values);
+// otherwise the tracked values that travelled with the blocks are used.
 // Returns the number of rotations this warp applied (identical in every lane).
 template <typename J, int NV, int K>
 __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int b, int rp, int t, int sweep,
-                                             J tol2, J tiny, int lane, int wid) {
+                                             J tol2, J tiny, int lane, int wid, bool refresh) {
   const int G = b / K;  // warps doing pair work (== warps in the block)
   auto col = [&](int c) { return sm + (int64_t)c * rp; };
   auto sidx = [&](int c) { return c < b ? c : 32 + (c - b); };
@@ -356,7 +358,7 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
   // (it was then verified orthogonal and has not changed since)
   auto fresh = [&](int st) { return sweep == 0 || st >= sweep - 1; };
   // fresh squared norms, K columns per warp at a time
-  for (int c0 = wid * K; c0 < 2 * b; c0 += G * K) {
+  for (int c0 = wid * K; refresh && c0 < 2 * b; c0 += G * K) {
     Col<J, NV> x[K];
     J nr[K];
 #pragma unroll
@@ -364,7 +366,7 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
 #pragma unroll
     for (int i = 0; i < K; ++i) nr[i] = dot_lane(x[i], x[i]);
     const J t = warp_sum_spread<J, K>(nr, lane);
-    if ((lane & (32 / K - 1)) == 0) s_nrm[c0 + lane / (32 / K)] = t;
+    if ((lane & (32 / K - 1)) == 0) s_nrm[sidx(c0 + lane / (32 / K))] = t;
   }
   __syncthreads();
   int rot = 0;
@@ -383,8 +385,8 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
         p1[i] = blk * b + circle_pos(b - 1 - k, st, b);
         x[i].load(col(p0[i]), lane);
         y[i].load(col(p1[i]), lane);
-        a[i] = s_nrm[p0[i]];
-        bn[i] = s_nrm[p1[i]];
+        a[i] = s_nrm[sidx(p0[i])];
+        bn[i] = s_nrm[sidx(p1[i])];
         act |= (fresh(s_stamp[sidx(p0[i])]) || fresh(s_stamp[sidx(p1[i])])) ? (1u << i) : 0u;
       }
       const unsigned r = step_pairs<J, NV, K, 0>(x, y, a, bn, xf, yf, act, tol2, tiny, lane);
@@ -394,8 +396,8 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
           x[i].store(col(p0[i]), lane);
           y[i].store(col(p1[i]), lane);
           if (lane == 0) {
-            s_nrm[p0[i]] = a[i];
-            s_nrm[p1[i]] = bn[i];
+            s_nrm[sidx(p0[i])] = a[i];
+            s_nrm[sidx(p1[i])] = bn[i];
             s_stamp[sidx(p0[i])] = sweep;
             s_stamp[sidx(p1[i])] = sweep;
           }
@@ -413,7 +415,7 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       x[i].load(col(xc + i), lane);
-      a[i] = s_nrm[xc + i];
+      a[i] = s_nrm[sidx(xc + i)];
       xf |= fresh(s_stamp[sidx(xc + i)]) ? 1u << i : 0u;
     }
     unsigned xdirty = 0;
@@ -425,7 +427,7 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
       const int yc = b + v * K;
 #pragma unroll
       for (int i = 0; i < K; ++i) {
-        bn[i] = s_nrm[yc + i];
+        bn[i] = s_nrm[sidx(yc + i)];
         yf |= fresh(s_stamp[sidx(yc + i)]) ? 1u << i : 0u;
       }
       unsigned ydirty = 0;
@@ -465,7 +467,7 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
         if ((ydirty >> i) & 1u) {
           y[i].store(col(yc + i), lane);
           if (lane == 0) {
-            s_nrm[yc + i] = bn[i];
+            s_nrm[sidx(yc + i)] = bn[i];
             s_stamp[sidx(yc + i)] = sweep;
           }
         }
@@ -478,7 +480,7 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
       if ((xdirty >> i) & 1u) {
         x[i].store(col(xc + i), lane);
         if (lane == 0) {
-          s_nrm[xc + i] = a[i];
+          s_nrm[sidx(xc + i)] = a[i];
           s_stamp[sidx(xc + i)] = sweep;
         }
       }
@@ -597,7 +599,7 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
   __shared__ int s_total;
   __shared__ int s_stop;
   __shared__ double s_tiny;
-  __shared__ J s_nrm[64];                       // squared norms of the 2b staged columns
+  __shared__ __align__(16) J s_nrm[3][64];      // tracked squared norms of the staged columns (per buffer)
   __shared__ __align__(16) int s_stamp[3][64];  // sweep of each staged column's last rotation (per buffer)
   __shared__ __align__(8) uint64_t s_full[3];   // per buffer: the incoming blocks have landed
 
@@ -663,7 +665,10 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
         }
         __syncthreads();
       }
-      const int rot = process_round<J, NV, PairK<J, NV>::K>(sm, s_nrm, st, b, rp, t, sweep, tol2, tiny, lane, wid);
+      // with the DSM exchange the tracked norms travel with the blocks and are refreshed
+      // once per sweep; through L2 they are recomputed every round
+      const int rot = process_round<J, NV, PairK<J, NV>::K>(sm, s_nrm[DSM ? cur : 0], st, b, rp, t, sweep, tol2,
+                                                            tiny, lane, wid, !DSM || t == 0);
       if (lane == 0 && rot) atomicAdd(&s_rot, rot);
       last_t = t;
       if (!DSM) {
@@ -683,7 +688,7 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
         if (pending) cluster_wait();  // every CTA has finished the previous round: buffer nxt is free everywhere
         __syncthreads();
         if (tid == 0) {
-          mbar_arrive_expect_tx(&s_full[nxt], 2u * (blk_bytes + 128u));
+          mbar_arrive_expect_tx(&s_full[nxt], 2u * (blk_bytes + 128u + 32u * (uint32_t)sizeof(J)));
           J* dst_buf = buffer(nxt);
           for (int half = 0; half < 2; ++half) {
             const int slot = half == 0 ? crank : nblk - 1 - crank;
@@ -695,6 +700,8 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
                       sm + (int64_t)half * b * rp, blk_bytes, mbar);
             bulk_push(cluster_addr(smem_addr(&s_stamp[nxt][to_half * 32]), to_cta), &s_stamp[cur][half * 32], 128u,
                       mbar);
+            bulk_push(cluster_addr(smem_addr(&s_nrm[nxt][to_half * 32]), to_cta), &s_nrm[cur][half * 32],
+                      32u * (uint32_t)sizeof(J), mbar);
           }
         }
         cluster_arrive();  // this round is computed (and its blocks are on their way)
