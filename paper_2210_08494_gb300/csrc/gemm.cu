@@ -170,20 +170,46 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmArgs g) {
 // product errors in a compensation term: s + c carries the dot product to
 // about u32^2 relative to sum |a_k b_k|.  The split partials are written as
 // double (s + c) and summed in FP64 by splitk_reduce.  Upper tiles only.
-struct Comp {
-  float s, c;
+// Two independent accumulators at once, on the packed FP32 instructions (each
+// lane rounded to nearest; explicit instructions, so no step is contracted into
+// an FMA or reassociated, which would break the error-free transformation):
+// s, c, a, b hold pairs; -p is formed by flipping the two sign bits (exact).
+struct Comp2 {
+  uint64_t s, c;
 };
-
-// explicit round-to-nearest intrinsics: the transformation is only error-free
-// if no step is contracted into an FMA or reassociated
-__device__ __forceinline__ void comp_fma(Comp& acc, float a, float b) {
-  const float p = __fmul_rn(a, b);
-  const float e = __fmaf_rn(a, b, -p);
-  const float t = __fadd_rn(acc.s, p);
-  const float z = __fsub_rn(t, acc.s);
-  const float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(t, z)), __fsub_rn(p, z));
+__device__ __forceinline__ uint64_t f2_add(uint64_t x, uint64_t y) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x), "l"(y));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t x, uint64_t y) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x), "l"(y));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t x, uint64_t y) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x), "l"(y));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t x, uint64_t y, uint64_t z) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(x), "l"(y), "l"(z));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void comp_fma2(Comp2& acc, uint64_t a, uint64_t b) {
+  const uint64_t p = f2_mul(a, b);
+  const uint64_t e = f2_fma(a, b, p ^ 0x8000000080000000ull);
+  const uint64_t t = f2_add(acc.s, p);
+  const uint64_t z = f2_sub(t, acc.s);
+  const uint64_t err = f2_add(f2_sub(acc.s, f2_sub(t, z)), f2_sub(p, z));
   acc.s = t;
-  acc.c = __fadd_rn(acc.c, __fadd_rn(err, e));
+  acc.c = f2_add(acc.c, f2_add(err, e));
 }
 
 __global__ void __launch_bounds__(NT) gram_comp_kernel(const GemmArgs g) {
@@ -197,11 +223,12 @@ __global__ void __launch_bounds__(NT) gram_comp_kernel(const GemmArgs g) {
   const int kb = blockIdx.z * g.k_chunk;
   const int ke = min(K, kb + g.k_chunk);
   const float* A = (const float*)g.A0;
-  Comp acc[4][4];
+  // acc2[i][h] carries outputs (i, j = 2h) and (i, j = 2h + 1) as packed pairs
+  Comp2 acc2[4][2];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = Comp{0.f, 0.f};
+    for (int h = 0; h < 2; ++h) acc2[i][h] = Comp2{0ull, 0ull};
   for (int kt = kb; kt < ke; kt += BKK) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -219,10 +246,13 @@ __global__ void __launch_bounds__(NT) gram_comp_kernel(const GemmArgs g) {
       for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
       for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      const uint64_t b2[2] = {f2_pack(b[0], b[1]), f2_pack(b[2], b[3])};
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 4; ++i) {
+        const uint64_t a2 = f2_pack(a[i], a[i]);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) comp_fma(acc[i][j], a[i], b[j]);
+        for (int h = 0; h < 2; ++h) comp_fma2(acc2[i][h], a2, b2[h]);
+      }
     }
     __syncthreads();
   }
@@ -232,7 +262,14 @@ __global__ void __launch_bounds__(NT) gram_comp_kernel(const GemmArgs g) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
-      if (m < g.M && n < g.N) P[(int64_t)m * g.N + n] = (double)acc[i][j].s + (double)acc[i][j].c;
+      float sv, cv, s2, c2;
+      asm("mov.b64 {%0, %1}, %2;" : "=f"(sv), "=f"(s2) : "l"(acc2[i][j >> 1].s));
+      asm("mov.b64 {%0, %1}, %2;" : "=f"(cv), "=f"(c2) : "l"(acc2[i][j >> 1].c));
+      if (j & 1) {
+        sv = s2;
+        cv = c2;
+      }
+      if (m < g.M && n < g.N) P[(int64_t)m * g.N + n] = (double)sv + (double)cv;
     }
 }
 
