@@ -450,6 +450,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     g.ldc = p.ldm;
     g.splits = gemm_pick_splits(k, n, d, 152);
     g.partial = part;
+    g.partial_bytes = p.part_bytes;
     PHASE(PH_PROJ, gemm_run(g, pr.t, pr.acc, pr.t, s));
     // P = X - U M  (d x n, K = k)
     GemmArgs h = gemm_base();
@@ -1065,6 +1066,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
       g.cs = cA;
       g.splits = gemm_pick_splits(kG, kA, dG, 152);
       g.partial = at<void>(ws, cap.o_part);
+      g.partial_bytes = partial_bytes(r_total(fG), r_total(fA), dG, es_of(pr.acc));
       PHASE(PH_APPLY_SMALL, gemm_run(g, pr.t, pr.acc, pr.t, s));
     }
     GemmArgs g = gemm_base();

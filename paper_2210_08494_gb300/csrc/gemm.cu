@@ -524,10 +524,10 @@ __global__ void __launch_bounds__(LNT, 2) sgemm_large_kernel(const GemmArgs g) {
   }
 }
 
-bool large_ok(const GemmArgs& g) {
+// operand layouts and alignment the 128 x 128 kernel accepts
+bool large_layout_ok(const GemmArgs& g) {
   auto al = [](const void* p) { return p == nullptr || ((uintptr_t)p % 16) == 0; };
   if (g.sym) return false;
-  if ((int64_t)g.M * g.N < 128 * 128 * 8) return false;  // small outputs: the 64 x 64 kernel
   // a 4-wide load along K must stay inside one K segment and 16-byte aligned: the
   // seam K0 a multiple of 4 when either operand is K-contiguous (M- and N-contiguous
   // operands load one K index at a time)
@@ -535,6 +535,11 @@ bool large_ok(const GemmArgs& g) {
   if (!al(g.A0) || !al(g.A1) || !al(g.B0) || !al(g.B1)) return false;
   if (g.lda0 % 4 || g.ldb0 % 4 || (g.K1 > 0 && (g.lda1 % 4 || g.ldb1 % 4))) return false;
   return true;
+}
+
+bool large_ok(const GemmArgs& g) {
+  if ((int64_t)g.M * g.N < 128 * 128 * 8) return false;  // small outputs: the 64 x 64 kernel
+  return large_layout_ok(g);
 }
 
 int run_large_f32(const GemmArgs& g, cudaStream_t s) {
@@ -652,6 +657,21 @@ int gemm_run(const GemmArgs& g, DType in_t, DType acc_t, DType out_t, cudaStream
         a.splits = (int)std::min<int64_t>(std::min<int64_t>(4, 304 / tiles), room);
       if (a.splits > 1 && room < a.splits) a.splits = (int)std::max<int64_t>(1, room);
       return run_large_f32(a, s);
+    }
+    // a small output over a long K (U^T X, U_G^T T1 at r = n = 256, K = d): the 128 x 128
+    // kernel split along K into enough pieces to fill the GPU, when the partial buffer
+    // holds them
+    const int K = g.K0 + g.K1;
+    if ((int64_t)g.M * g.N >= 128 * 128 * 2 && K >= 2048 && g.partial && large_layout_ok(g)) {
+      const int64_t tiles = ceil_div(g.M, LBM) * ceil_div(g.N, LBN);
+      const int64_t room = (int64_t)(g.partial_bytes / ((size_t)g.M * g.N * sizeof(float)));
+      const int64_t sp = std::min<int64_t>(std::min<int64_t>(room, 32),
+                                           std::min<int64_t>(K / 128, ceil_div(2 * 152, tiles)));
+      if (sp >= 8) {
+        GemmArgs a = g;
+        a.splits = (int)sp;
+        return run_large_f32(a, s);
+      }
     }
     return run_typed<float, float, float>(g, s);
   }
