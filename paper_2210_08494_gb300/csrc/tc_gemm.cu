@@ -10,15 +10,16 @@
 //
 // Tile: 128 x 128 outputs per CTA (one tcgen05.mma.cta_group::1 of M = 128,
 // N = 128 per K step of 16), K staged 64 at a time in two shared-memory buffers.
-// Four warps convert and store the next K block while the tensor core works on
+// Eight warps convert and store the next K block while the tensor core works on
 // the current one; one thread issues the MMAs and commits them to the buffer's
 // mbarrier, which releases the buffer for reuse.  The accumulator lives in 128
 // TMEM columns; the epilogue reads it back with tcgen05.ld (warp w reads TMEM
-// lanes 32w .. 32w + 31, i.e. output rows) into a shared-memory tile, from
-// which rows (row-major C, split-K partials) or columns (column-major C) leave
-// with coalesced accesses after the scaling; splitk_reduce sums partials in a
-// fixed order.
-//
+// lanes 32 (w mod 4) .. 32 (w mod 4) + 31, i.e. output rows, the two warps of a
+// quadrant one half of the columns each) into a shared-memory tile, from which
+// rows (row-major C, split-K partials) or columns (column-major C) leave with
+// coalesced accesses after the scaling; splitk_reduce sums partials in a fixed
+// order.  Two CTAs per SM (at most 128 registers per thread).
+
 // Shared-memory operand layout: K-major, no swizzle.  Each K step of 16 is a
 // 128 x 16 sub-tile (4 KB) built from 8 x 16-byte "core matrices" (8 rows of 8
 // BF16): core matrices adjacent in K are 128 bytes apart (leading byte offset),
@@ -35,7 +36,7 @@ namespace bkfac {
 namespace {
 
 constexpr int TM = 128, TN = 128;  // output tile
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;  // eight warps: two per TMEM lane quadrant in the epilogue
 constexpr int SUB_BYTES = 4096;  // one 128-row operand sub-tile: the K of one MMA (32 bytes per row)
 constexpr int TMEM_COLS = 128;
 constexpr int TLD = TN + 1;  // leading dimension of the staged output tile (floats)
@@ -358,7 +359,7 @@ __device__ __forceinline__ void store_operand(const GemmArgs& g, unsigned char* 
 }
 
 template <bool X3>
-__global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const GemmArgs g) {
+__global__ void __launch_bounds__(TC_THREADS, 2) tc_gemm_kernel(const GemmArgs g) {
   using Md = TcMode<X3>;
   constexpr int TK = Md::TK, STAGE_BYTES = Md::STAGE_BYTES;
   extern __shared__ __align__(16) unsigned char tc_smem_raw[];  // only 16 bytes are guaranteed
@@ -444,9 +445,13 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const GemmArgs g) {
     // run over rows or over columns); the operand buffers are free now
     float* T = reinterpret_cast<float*>(tc_smem);
     {
-      const int row = wid * 32 + lane;
-      const uint32_t trow = tmem + ((uint32_t)(wid * 32) << 16);
-      for (int c0 = 0; c0 < TN; c0 += 16) {
+      // a warp reaches the TMEM lanes of its quadrant (warp id mod 4): rows 32 q ..
+      // 32 q + 31; the warps sharing a quadrant split the columns
+      constexpr int NW = TC_THREADS / 32, CPW = TN / (NW / 4);
+      const int q = wid & 3, c_begin = (wid >> 2) * CPW;
+      const int row = q * 32 + lane;
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+      for (int c0 = c_begin; c0 < c_begin + CPW; c0 += 16) {
         float v[16];
         if (nk > 0) {
           tc_ld16(trow + (uint32_t)c0, v);
