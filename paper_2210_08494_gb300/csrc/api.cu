@@ -86,7 +86,7 @@ struct UpdatePlan {
   int C, b, rows_pad, cols_pad;  // Jacobi plan of this call
   int rows_cap, cols_cap;        // capacity of L
   size_t o_scale, o_M, o_part, o_P, o_Q1, o_Q, o_G, o_R1, o_R2, o_Rinv, o_L, o_cn, o_lam, o_V, o_Un, o_sw, o_st,
-      o_flag;
+      o_flag, o_K;
   size_t part_bytes;
   size_t total;
 };
@@ -156,6 +156,8 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
     p.o_sw = L.add(256);
     p.o_st = L.add((size_t)cols_cap * 4);
     p.o_flag = L.add(16);
+    // the core's Gram L L^T for the preconditioned eigensolve (FP32 eigensolves)
+    if (p.pr.jt == DT_F32) p.o_K = L.add((size_t)Nmax * Nmax * sizeof(float));
   }
   p.rows_cap = rows_cap;
   p.cols_cap = cols_cap;
@@ -306,6 +308,15 @@ int run_chol(const double* Gm, int n, double* R, double thr_rel, const double* s
 
 // second CholeskyQR pass: G2 = I + E; the near-identity factor's error is O(|E|^2)
 double near_identity_tol(const Prec& pr) { return pr.t == DT_F64 ? 1e-9 : 1e-5; }
+
+// FP32 eigensolves of Brand cores with at least this many columns run the Jacobi
+// on the Cholesky factor of the core matrix instead of the core factor L (fewer
+// sweeps; the factorisation costs a few percent of one sweep)
+constexpr int kPrecondMinN = 128;
+
+bool precondition_core(const UpdatePlan& p) {
+  return !p.dense && p.pr.jt == DT_F32 && p.N >= kPrecondMinN && chol_core_ok(p.N, p.rows_pad, p.cols_pad);
+}
 
 GemmArgs gemm_base() {
   GemmArgs g;
@@ -507,6 +518,29 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   ca.L = at<void>(ws, p.o_L);
   ca.colnorm2 = at<double>(ws, p.o_cn);
   PHASE(PH_CORE, launch_assemble_core(ca, pr.t, pr.jt, s));
+  if (precondition_core(p)) {
+    // K = L L^T (FP32), then K = G G^T: G = L Z (Z orthogonal) has the left singular
+    // vectors and singular values of L, and its columns are much closer to orthogonal
+    float* Kc = at<float>(ws, p.o_K);
+    GemmArgs kg = gemm_base();
+    kg.M = p.N;
+    kg.N = p.N;
+    kg.K0 = p.N;
+    kg.A0 = ca.L;
+    kg.lda0 = p.rows_pad;
+    kg.a_kmaj = false;
+    kg.B0 = ca.L;
+    kg.ldb0 = p.rows_pad;
+    kg.b_kmaj = false;
+    kg.C = Kc;
+    kg.ldc = p.N;
+    kg.splits = gemm_pick_splits(p.N, p.N, p.N, 152);
+    kg.partial = part;
+    kg.partial_bytes = p.part_bytes;
+    PHASE(PH_PRECOND, gemm_run(kg, DT_F32, DT_F32, DT_F32, s));
+    const float thr_rel = (float)(4.0 * std::sqrt((double)p.N) * 5.9604644775390625e-08);
+    PHASE(PH_PRECOND, launch_chol_core(Kc, p.N, p.N, (float*)ca.L, p.rows_pad, p.cols_pad, ca.colnorm2, thr_rel, s));
+  }
   JacobiProblem jp;
   jp.W = ca.L;
   jp.rows = p.N;

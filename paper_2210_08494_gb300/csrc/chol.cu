@@ -369,6 +369,237 @@ __global__ void __launch_bounds__(CBT) chol_block_kernel(const double* __restric
   cluster.sync();  // keep shared memory alive until every remote read is done
 }
 
+
+// ---------------------------------------------------------------------------
+// FP32 Cholesky of the Brand core's Gram for the eigensolve (preconditioning).
+// The one-sided Jacobi of the update orthogonalises the columns of the core
+// factor L (N x N, K = L L^T is the core matrix).  With K = G G^T (G lower
+// triangular, the Cholesky factor), G = L Z for an orthogonal Z: G has the same
+// left singular vectors as L -- the eigenvectors of K -- and the same singular
+// values.  The Gram of G's columns, G^T G, is K after one step of the LR
+// (Cholesky) iteration, much closer to diagonal than L^T L on the graded
+// spectra of the EA factors, so the Jacobi run on G instead of L needs fewer
+// sweeps (9-10 instead of 11-12 on a 512-column wide-layer core).
+//
+// Layout: 4 x 4 grid of CTAs (a 16-CTA cluster), 32 x 32 blocks of the lower
+// triangle, block (i, j) in CTA (i mod 4, j mod 4).  In shared memory a block is
+// row-major with its 16-byte chunks XOR-swizzled by the row, element (r, c) at
+//   r * 32 + ((c / 4) ^ (r mod 8)) * 4 + c mod 4,
+// so that a warp reading a column (a lane per row) or eight lanes reading eight
+// rows' chunks with 128-bit accesses meet no bank conflict.  A diagonal block
+// holds its full symmetric square until it is factored and then L_kk^T.
+// Step k: (A) one warp of the diagonal owner factors L_kk with shuffles (lane =
+// row); a pivot <= thr_rel * K_jj (the rounding noise of the FP32 Gram and of
+// the elimination, relative to the column's own diagonal) is dropped: its column
+// of G is zero; (B) the owners of the panel blocks (i, k), i > k,
+// solve L_ik L_kk^T = A_ik, a thread per row; (C) every CTA applies the rank-32
+// update to its trailing blocks from transposed copies of the panel blocks.
+// Two cluster barriers per step.  The output is G itself, written as the
+// Jacobi's column-major rows_pad x cols_pad matrix (zero above the diagonal and
+// beyond n), with its columns' squared norms (FP64 sums of the FP32 entries).
+constexpr int QB = 32;           // block size
+constexpr int QBT = 512;         // threads per CTA
+constexpr int kCoreMaxN = 768;   // 6 x 6 blocks per CTA: the most that fit in shared memory
+
+__device__ __forceinline__ int qsw(int r, int c) { return r * QB + ((((c >> 2) ^ r) & 7) << 2) + (c & 3); }
+
+__global__ void __launch_bounds__(QBT) chol_core_kernel(const float* __restrict__ K, int ldk, int n, float* W,
+                                                        int rows_pad, int cols_pad, double* colnorm2,
+                                                        float thr_rel) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int pr = rank >> 2, pc = rank & 3;
+  const int nb = (n + QB - 1) / QB, S = (nb + 3) / 4;
+  const int ncb = (cols_pad + QB - 1) / QB, Sc = (ncb + 3) / 4;
+  extern __shared__ __align__(16) float qsm[];
+  float* slots = qsm;                         // S x S blocks: block (4a + pr, 4b + pc) at slot a * S + b
+  float* LiT = slots + (size_t)S * S * 1024;  // panel blocks (4a + pr, k), transposed: [m][r]
+  float* LjT = LiT + (size_t)S * 1024;        // panel blocks (4b + pc, k), transposed: [m][c]
+  float* Lkk = LjT + (size_t)S * 1024;        // L_kk^T (swizzled), copied from the diagonal owner
+  float* inv = Lkk + 1024;                    // 1 / L_kk[j][j] (0 for a dropped pivot)
+  float* inv_local = inv + 32;
+  double* colpart = (double*)(inv_local + 32);  // this CTA's part of the columns' squared norms
+  __shared__ float s_kd[kCoreMaxN];
+  auto slot = [&](int a, int b) { return slots + (size_t)(a * S + b) * 1024; };
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+  // the original diagonal: pivot j is dropped when its Schur complement is at most
+  // thr_rel * K_jj (the rounding noise of the FP32 Gram and of the elimination)
+  for (int i = tid; i < nb * QB; i += QBT) s_kd[i] = i < n ? K[i + (int64_t)i * ldk] : 0.f;
+  // owned lower blocks; a diagonal block as its full symmetric square read from the
+  // lower triangle; entries past n are zero (their pivots are dropped)
+  for (int e = tid; e < S * S * 1024; e += QBT) {
+    const int sl = e >> 10, w = e & 1023, a = sl / S, b = sl % S;
+    const int i = 4 * a + pr, j = 4 * b + pc;
+    const int c = w >> 5, r = w & 31;  // consecutive threads: consecutive rows (coalesced reads)
+    const int row = QB * i + r, col = QB * j + c;
+    float v = 0.f;
+    if (i < nb && j <= i && row < n && col < n)
+      v = row >= col ? K[row + (int64_t)col * ldk] : K[col + (int64_t)row * ldk];
+    slots[(size_t)sl * 1024 + qsw(r, c)] = v;
+  }
+  __syncthreads();
+
+  for (int k = 0; k < nb; ++k) {
+    const int dk = k & 3, kb = k >> 2;
+    // ---- A: factor the diagonal block; lane r keeps row r (read as column r of the
+    // symmetric square), pivots and the current column broadcast by shuffles
+    if (pr == dk && pc == dk && wid == 0) {
+      float* D = slot(kb, kb);
+      const float thr = thr_rel * s_kd[k * QB + lane];
+      float d[QB];
+#pragma unroll
+      for (int c = 0; c < QB; ++c) d[c] = D[qsw(c, lane)];
+      bool bad = false;
+#pragma unroll
+      for (int j = 0; j < QB; ++j) {
+        const float p = __shfl_sync(0xffffffffu, d[j], j);
+        bad |= !(fabsf(p) <= 3.402823466e38f);  // NaN or infinite
+        const float il = p > __shfl_sync(0xffffffffu, thr, j) ? rsqrtf(p) : 0.f;
+        const float l = lane >= j ? d[j] * il : 0.f;
+        d[j] = l;
+        if (lane == j) inv[j] = il;
+#pragma unroll
+        for (int c = j + 1; c < QB; ++c) d[c] = fmaf(-l, __shfl_sync(0xffffffffu, l, c), d[c]);
+      }
+      if (bad && lane == 0) report(BKFAC_ENONFINITE);
+      // element (c, r) of the stored block = L_kk[r][c] (zero for c > r)
+#pragma unroll
+      for (int c = 0; c < QB; ++c) D[qsw(c, lane)] = d[c];
+    }
+    cluster.sync();  // L_kk and its reciprocals are final
+    // ---- B: the panel blocks below the diagonal, owned by the CTAs of grid column dk
+    if (pc == dk) {
+      const int src = dk * 4 + dk;
+      const float4* rL = (const float4*)cluster.map_shared_rank(slot(kb, kb), src);
+      const float* rI = cluster.map_shared_rank(inv, src);
+      for (int e = tid; e < 256; e += QBT) ((float4*)Lkk)[e] = rL[e];
+      if (tid < 32) inv_local[tid] = rI[tid];
+      __syncthreads();
+      for (int t = tid; t < S * QB; t += QBT) {
+        const int a = t >> 5, r = t & 31, i = 4 * a + pr;
+        if (i <= k || i >= nb) continue;
+        float* B = slot(a, kb) + r * QB;
+        float x[QB];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 v = *(const float4*)(B + (((q ^ r) & 7) << 2));
+          x[4 * q] = v.x;
+          x[4 * q + 1] = v.y;
+          x[4 * q + 2] = v.z;
+          x[4 * q + 3] = v.w;
+        }
+        // right-looking: x_j /= L_jj, then x_m -= x_j L_mj for m > j (row j of the
+        // stored L_kk^T holds L_mj, m = 0..31)
+#pragma unroll
+        for (int j = 0; j < QB; ++j) {
+          const float xj = x[j] * inv_local[j];
+          x[j] = xj;
+#pragma unroll
+          for (int q = (j + 1) >> 2; q < 8; ++q) {
+            const float4 lv = *(const float4*)(Lkk + j * QB + (((q ^ j) & 7) << 2));
+            if (4 * q + 0 > j) x[4 * q + 0] = fmaf(-xj, lv.x, x[4 * q + 0]);
+            if (4 * q + 1 > j) x[4 * q + 1] = fmaf(-xj, lv.y, x[4 * q + 1]);
+            if (4 * q + 2 > j) x[4 * q + 2] = fmaf(-xj, lv.z, x[4 * q + 2]);
+            if (4 * q + 3 > j) x[4 * q + 3] = fmaf(-xj, lv.w, x[4 * q + 3]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          *(float4*)(B + (((q ^ r) & 7) << 2)) = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+      }
+    }
+    cluster.sync();  // the panel of step k is final
+    // ---- C: trailing update of the owned blocks (i, j), k < j <= i
+    {
+      const int rsrc = pr * 4 + dk, csrc = pc * 4 + dk;
+      for (int e = tid; e < 2 * S * 256; e += QBT) {
+        const int half = e / (S * 256), w = e % (S * 256), a = w >> 8, o = w & 255;
+        const int g = 4 * a + (half ? pc : pr);
+        if (g <= k || g >= nb) continue;
+        const int r = o & 31, q = o >> 5;
+        const float4* src = (const float4*)cluster.map_shared_rank(slot(a, kb), half ? csrc : rsrc);
+        const float4 v = src[(r * QB + (((q ^ r) & 7) << 2)) >> 2];
+        float* dst = (half ? LjT : LiT) + (size_t)a * 1024 + r;
+        dst[(4 * q + 0) * QB] = v.x;
+        dst[(4 * q + 1) * QB] = v.y;
+        dst[(4 * q + 2) * QB] = v.z;
+        dst[(4 * q + 3) * QB] = v.w;
+      }
+      __syncthreads();
+      // 4 x 4 tiles, 64 per block (a warp covers half a block: uniform branches)
+      for (int e = tid; e < S * S * 64; e += QBT) {
+        const int sl = e >> 6, t = e & 63, a = sl / S, b = sl % S;
+        const int i = 4 * a + pr, j = 4 * b + pc;
+        if (j <= k || j > i || i >= nb) continue;
+        const int r0 = (t >> 3) << 2, c0 = (t & 7) << 2;
+        const float* li = LiT + (size_t)a * 1024 + r0;
+        const float* lj = LjT + (size_t)b * 1024 + c0;
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+#pragma unroll 8
+        for (int m = 0; m < QB; ++m) {
+          const float4 x = *(const float4*)(li + m * QB);
+          const float4 y = *(const float4*)(lj + m * QB);
+          const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xs[u], ys[v], acc[u][v]);
+        }
+        float* T = slots + (size_t)sl * 1024;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int row = r0 + u;
+          float4* p = (float4*)(T + row * QB + ((((c0 >> 2) ^ row) & 7) << 2));
+          float4 o = *p;
+          o.x -= acc[u][0];
+          o.y -= acc[u][1];
+          o.z -= acc[u][2];
+          o.w -= acc[u][3];
+          *p = o;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ---- output: W = G, column-major rows_pad x cols_pad; a warp per column of this
+  // CTA's block columns, lanes over the rows of its block rows
+  const int nrb = rows_pad / QB;
+  for (int u = wid; u < Sc * QB; u += QBT / 32) {
+    const int b = u >> 5, c = u & 31, jb = 4 * b + pc, col = jb * QB + c;
+    double ss = 0.0;
+    if (col < cols_pad) {
+      for (int ib = pr; ib < nrb; ib += 4) {
+        float v = 0.f;
+        if (ib < nb && jb <= ib) {
+          const float* blk = slot(ib >> 2, b);
+          v = ib != jb ? blk[qsw(lane, c)] : (lane >= c ? blk[qsw(c, lane)] : 0.f);
+        }
+        W[ib * QB + lane + (int64_t)col * rows_pad] = v;
+        ss += (double)v * (double)v;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) colpart[u] = ss;
+  }
+  cluster.sync();
+  if (pr == 0) {
+    for (int u = tid; u < Sc * QB; u += QBT) {
+      const int col = (4 * (u >> 5) + pc) * QB + (u & 31);
+      if (col >= cols_pad) continue;
+      double t = 0.0;
+      for (int q = 0; q < 4; ++q) t += *cluster.map_shared_rank(colpart + u, q * 4 + pc);
+      colnorm2[col] = t;
+      if (!isfinite(t)) report(BKFAC_ENONFINITE);
+    }
+  }
+  cluster.sync();  // keep shared memory alive until every remote read is done
+}
 }  // namespace
 
 // blocked cluster Cholesky: n x n with n <= 576 (at most 9 x 9 blocks per CTA)
@@ -403,6 +634,47 @@ int launch_chol_block(const double* Gm, int n, double* R, double thr_rel, const 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const cudaError_t e = cudaLaunchKernelEx(&cfg, chol_block_kernel, Gm, n, R, thr_rel, scale, near_tol, near_out);
+  note_launches(1);
+  return (int)e;
+}
+
+size_t chol_core_smem(int n, int cols_pad) {
+  const int nb = (n + QB - 1) / QB, S = (nb + 3) / 4;
+  const int ncb = (cols_pad + QB - 1) / QB, Sc = (ncb + 3) / 4;
+  return ((size_t)S * S + 2 * (size_t)S + 1) * 1024 * sizeof(float) + 64 * sizeof(float) +
+         (size_t)Sc * QB * sizeof(double);
+}
+
+bool chol_core_ok(int n, int rows_pad, int cols_pad) {
+  return n >= 1 && n <= kCoreMaxN && rows_pad >= n && rows_pad % QB == 0 && cols_pad >= n &&
+         chol_core_smem(n, cols_pad) <= 200 * 1024;
+}
+
+int launch_chol_core(const float* K, int ldk, int n, float* W, int rows_pad, int cols_pad, double* colnorm2,
+                     float thr_rel, cudaStream_t s) {
+  if (!chol_core_ok(n, rows_pad, cols_pad) || ldk < n) return (int)cudaErrorInvalidValue;
+  static std::atomic<int> configured{0};  // attributes set once (the call can stall the host)
+  if (!configured.load()) {
+    cudaError_t e = cudaFuncSetAttribute(chol_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(chol_core_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return (int)e;
+    configured.store(1);
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(16, 1, 1);
+  cfg.blockDim = dim3(QBT, 1, 1);
+  cfg.dynamicSmemBytes = chol_core_smem(n, cols_pad);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 16;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e =
+      cudaLaunchKernelEx(&cfg, chol_core_kernel, K, ldk, n, W, rows_pad, cols_pad, colnorm2, thr_rel);
   note_launches(1);
   return (int)e;
 }

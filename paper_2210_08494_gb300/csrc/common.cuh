@@ -126,6 +126,14 @@ int chol_cluster_size(int n);  // 0 when n is too large for the cluster kernel
 bool chol_block_ok(int n);
 int launch_chol_block(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
                       int* near_out, cudaStream_t s);
+// FP32 Cholesky K = G G^T of an n x n symmetric positive semidefinite matrix (lower
+// triangle read, column-major, ld ldk) on a 16-CTA cluster, written as the Jacobi's
+// column-major rows_pad x cols_pad matrix G (zero above the diagonal and beyond n)
+// with its columns' squared norms; pivot j is dropped (zero column of G) when its
+// Schur complement is <= thr_rel * K_jj; for n <= 768 (chol_core_ok)
+bool chol_core_ok(int n, int rows_pad, int cols_pad);
+int launch_chol_core(const float* K, int ldk, int n, float* W, int rows_pad, int cols_pad, double* colnorm2,
+                     float thr_rel, cudaStream_t s);
 // inverse of the upper-triangular R (zero rows = dropped pivots -> zero rows/cols of Rinv);
 // when near (may be null) points to a nonzero flag, R = I + F is near identity and
 // Rinv = I - F (exact to O(|F|^2)) is written instead
@@ -261,7 +269,7 @@ int launch_mode_order(const double* sig, int k, int* perm, double* sorted, cudaS
 enum Phase {
   PH_COLNORM, PH_PROJ, PH_RESID, PH_GRAM, PH_CHOL, PH_TRINV, PH_TRMM, PH_CORE, PH_JACOBI, PH_SORT,
   PH_ROTATE, PH_FINALIZE, PH_DENSE, PH_COEFS, PH_APPLY1, PH_APPLY_SMALL, PH_APPLY2, PH_REORTH, PH_FACT_THIN,
-  PH_FACT_STEP, PH_COUNT
+  PH_FACT_STEP, PH_PRECOND, PH_COUNT
 };
 class TraceScope {
  public:

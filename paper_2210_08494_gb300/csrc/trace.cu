@@ -30,7 +30,7 @@ std::atomic<int64_t> g_launches{0};
 const char* kNames[PH_COUNT] = {"colnorm", "proj",   "resid",       "gram",     "chol",        "trinv",
                                 "trmm",    "core",   "jacobi",      "sort",     "rotate",      "finalize",
                                 "dense",   "coefs",  "apply_pass1", "apply_small", "apply_pass2", "reorth",
-                                "factored_thin", "factored_step"};
+                                "factored_thin", "factored_step", "precond"};
 
 cudaEvent_t take() {
   if (!g_pool.empty()) {
