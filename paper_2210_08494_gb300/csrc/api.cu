@@ -309,6 +309,22 @@ int run_chol(const double* Gm, int n, double* R, double thr_rel, const double* s
 // second CholeskyQR pass: G2 = I + E; the near-identity factor's error is O(|E|^2)
 double near_identity_tol(const Prec& pr) { return pr.t == DT_F64 ? 1e-9 : 1e-5; }
 
+// The Cholesky factorisations of CholeskyQR2: FP64 for the FP64 path; for the FP32
+// and mixed paths the FP64-accurate Gram is factored in FP32 on the cluster (FP64
+// runs at 1/64 of the FP32 rate on this GPU), and a pivot is also dropped when its
+// Schur complement is within the FP32 elimination's rounding noise of its diagonal,
+// 4 sqrt(n) u_32 G_jj: such a direction is numerically dependent at FP32 precision
+// and its orthogonalisation would be noise.  The second pass restores
+// orthonormality to the working precision as before.
+int run_chol_qr(const Prec& pr, const double* Gm, int n, double* R, double thr_abs, const double* scale,
+                double near_tol, int* near, cudaStream_t s) {
+  if (pr.t != DT_F64 && chol_r32_ok(n)) {
+    const float thr_rel = (float)(4.0 * std::sqrt((double)n) * 5.9604644775390625e-08);
+    return launch_chol_r32(Gm, n, R, thr_rel, thr_abs, scale, near_tol, near, s);
+  }
+  return run_chol(Gm, n, R, thr_abs, scale, near_tol, near, s);
+}
+
 // FP32 eigensolves of Brand cores with at least this many columns run the Jacobi
 // on the Cholesky factor of the core matrix instead of the core factor L (fewer
 // sweeps; the factorisation costs a few percent of one sweep)
@@ -493,12 +509,12 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   const double thr1 = pr.bf16 ? (2.0 * ue) * (2.0 * ue) : (64.0 * ue) * (64.0 * ue);
   const double thr2 = (64.0 * pr.u_t) * (64.0 * pr.u_t);
   PHASE(PH_GRAM, run_gram(Pp, ldp, d, n, pr, Gm, part, s));
-  PHASE(PH_CHOL, run_chol(Gm, n, R1, thr1, scale, 0.0, nullptr, s));
+  PHASE(PH_CHOL, run_chol_qr(pr, Gm, n, R1, thr1, scale, 0.0, nullptr, s));
   PHASE(PH_TRINV, launch_trinv(R1, n, Rinv, pr.t, nullptr, s));
   PHASE(PH_TRMM, run_trmm(Pp, ldp, d, n, Rinv, pr, Q1, p.ldq, part, p.part_bytes, s));
   PHASE(PH_GRAM, run_gram(Q1, p.ldq, d, n, pr, Gm, part, s));
   int* near = at<int>(ws, p.o_flag);
-  PHASE(PH_CHOL, run_chol(Gm, n, R2, thr2, nullptr, near_identity_tol(pr), near, s));
+  PHASE(PH_CHOL, run_chol_qr(pr, Gm, n, R2, thr2, nullptr, near_identity_tol(pr), near, s));
   PHASE(PH_TRINV, launch_trinv(R2, n, Rinv, pr.t, near, s));
   PHASE(PH_TRMM, run_trmm(Q1, p.ldq, d, n, Rinv, pr, Q, p.ldq, part, p.part_bytes, s));
   // core factor L and its Jacobi eigensolve
@@ -853,11 +869,11 @@ int run_orth(const void* Y, int d, int l, const RsvdPlan& p, void* ws, void* Q, 
   const double thr2 = (64.0 * pr.u_t) * (64.0 * pr.u_t);
   PHASE(PH_COLNORM, launch_colnorm_max(Y, p.ldq, d, l, pr.t, scale, s));
   PHASE(PH_GRAM, run_gram(Y, p.ldq, d, l, pr, Gm, part, s));
-  PHASE(PH_CHOL, run_chol(Gm, l, R1, thr1, scale, 0.0, nullptr, s));
+  PHASE(PH_CHOL, run_chol_qr(pr, Gm, l, R1, thr1, scale, 0.0, nullptr, s));
   PHASE(PH_TRINV, launch_trinv(R1, l, Rinv, pr.t, nullptr, s));
   PHASE(PH_TRMM, run_trmm(Y, p.ldq, d, l, Rinv, pr, Q1, p.ldq, part, p.part_bytes, s));
   PHASE(PH_GRAM, run_gram(Q1, p.ldq, d, l, pr, Gm, part, s));
-  PHASE(PH_CHOL, run_chol(Gm, l, R2, thr2, nullptr, near_identity_tol(pr), near, s));
+  PHASE(PH_CHOL, run_chol_qr(pr, Gm, l, R2, thr2, nullptr, near_identity_tol(pr), near, s));
   PHASE(PH_TRINV, launch_trinv(R2, l, Rinv, pr.t, near, s));
   PHASE(PH_TRMM, run_trmm(Q1, p.ldq, d, l, Rinv, pr, Q, p.ldq, part, p.part_bytes, s));
   return BKFAC_OK;

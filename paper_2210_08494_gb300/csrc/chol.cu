@@ -371,44 +371,56 @@ __global__ void __launch_bounds__(CBT) chol_block_kernel(const double* __restric
 
 
 // ---------------------------------------------------------------------------
-// FP32 Cholesky of the Brand core's Gram for the eigensolve (preconditioning).
-// The one-sided Jacobi of the update orthogonalises the columns of the core
-// factor L (N x N, K = L L^T is the core matrix).  With K = G G^T (G lower
-// triangular, the Cholesky factor), G = L Z for an orthogonal Z: G has the same
-// left singular vectors as L -- the eigenvectors of K -- and the same singular
-// values.  The Gram of G's columns, G^T G, is K after one step of the LR
-// (Cholesky) iteration, much closer to diagonal than L^T L on the graded
-// spectra of the EA factors, so the Jacobi run on G instead of L needs fewer
-// sweeps (9-10 instead of 11-12 on a 512-column wide-layer core).
+// FP32 blocked Cholesky K = G G^T on a 16-CTA cluster, for two uses:
 //
-// Layout: 4 x 4 grid of CTAs (a 16-CTA cluster), 32 x 32 blocks of the lower
-// triangle, block (i, j) in CTA (i mod 4, j mod 4).  In shared memory a block is
-// row-major with its 16-byte chunks XOR-swizzled by the row, element (r, c) at
+// (1) The eigensolve of the Brand core (W mode).  The one-sided Jacobi of the
+// update orthogonalises the columns of the core factor L (N x N, K = L L^T is
+// the core matrix).  With K = G G^T (G lower triangular), G = L Z for an
+// orthogonal Z: G has the same left singular vectors as L -- the eigenvectors of
+// K -- and the same singular values.  The Gram of G's columns, G^T G, is K after
+// one step of the LR (Cholesky) iteration, much closer to diagonal than L^T L on
+// the graded spectra of the EA factors, so the Jacobi run on G instead of L
+// needs fewer sweeps (9-10 instead of 11-12 on a 512-column wide-layer core).
+// G is written as the Jacobi's column-major rows_pad x cols_pad matrix (zero
+// above the diagonal and beyond n) with its columns' squared norms (FP64 sums
+// of the FP32 entries).
+//
+// (2) The CholeskyQR2 passes of the FP32 and mixed-precision paths (R mode): the
+// FP64-accurate Gram of the residual is factored in FP32 and R = G^T is written
+// as an n x n column-major FP64 upper triangle.  With near_tol > 0 the
+// near-identity test of the second pass runs first (on the FP64 Gram) and, when
+// every entry passes, R = I + Phi(E) is written instead of factoring (as in the
+// FP64 kernels above).
+//
+// Layout: 4 x 4 grid of CTAs, 32 x 32 blocks of the lower triangle, block (i, j)
+// in CTA (i mod 4, j mod 4).  In shared memory a block is row-major with its
+// 16-byte chunks XOR-swizzled by the row, element (r, c) at
 //   r * 32 + ((c / 4) ^ (r mod 8)) * 4 + c mod 4,
 // so that a warp reading a column (a lane per row) or eight lanes reading eight
 // rows' chunks with 128-bit accesses meet no bank conflict.  A diagonal block
 // holds its full symmetric square until it is factored and then L_kk^T.
 // Step k: (A) one warp of the diagonal owner factors L_kk with shuffles (lane =
-// row); a pivot <= thr_rel * K_jj (the rounding noise of the FP32 Gram and of
-// the elimination, relative to the column's own diagonal) is dropped: its column
-// of G is zero; (B) the owners of the panel blocks (i, k), i > k,
-// solve L_ik L_kk^T = A_ik, a thread per row; (C) every CTA applies the rank-32
-// update to its trailing blocks from transposed copies of the panel blocks.
-// Two cluster barriers per step.  The output is G itself, written as the
-// Jacobi's column-major rows_pad x cols_pad matrix (zero above the diagonal and
-// beyond n), with its columns' squared norms (FP64 sums of the FP32 entries).
+// row); pivot j is dropped (its column of G is zero) when its Schur complement
+// is at most max(thr_rel * K_jj, thr_abs * scale): thr_rel * K_jj is the rounding
+// noise of the FP32 elimination relative to the column's own diagonal, thr_abs
+// * scale the caller's absolute threshold; (B) the owners of the panel blocks
+// (i, k), i > k, solve L_ik L_kk^T = A_ik, a thread per row; (C) every CTA
+// applies the rank-32 update to its trailing blocks from transposed copies of
+// the panel blocks.  Two cluster barriers per step.
 constexpr int QB = 32;           // block size
 constexpr int QBT = 512;         // threads per CTA
 constexpr int kCoreMaxN = 768;   // 6 x 6 blocks per CTA: the most that fit in shared memory
 
 __device__ __forceinline__ int qsw(int r, int c) { return r * QB + ((((c >> 2) ^ r) & 7) << 2) + (c & 3); }
 
-__global__ void __launch_bounds__(QBT) chol_core_kernel(const float* __restrict__ K, int ldk, int n, float* W,
-                                                        int rows_pad, int cols_pad, double* colnorm2,
-                                                        float thr_rel) {
+template <typename TK, bool RM>
+__global__ void __launch_bounds__(QBT) chol_core_kernel(const CoreCholArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int pr = rank >> 2, pc = rank & 3;
+  const int n = a.n, rows_pad = a.rows_pad, cols_pad = a.cols_pad;
+  const int64_t ldk = a.ldk;
+  const TK* __restrict__ K = (const TK*)a.K;
   const int nb = (n + QB - 1) / QB, S = (nb + 3) / 4;
   const int ncb = (cols_pad + QB - 1) / QB, Sc = (ncb + 3) / 4;
   extern __shared__ __align__(16) float qsm[];
@@ -420,33 +432,64 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const float* __restrict_
   float* inv_local = inv + 32;
   double* colpart = (double*)(inv_local + 32);  // this CTA's part of the columns' squared norms
   __shared__ float s_kd[kCoreMaxN];
-  auto slot = [&](int a, int b) { return slots + (size_t)(a * S + b) * 1024; };
+  __shared__ int s_flag[2];  // near identity: [0] this CTA's blocks, [1] the cluster's decision
+  auto slot = [&](int ia, int ib) { return slots + (size_t)(ia * S + ib) * 1024; };
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const float thr_abs = (float)(a.thr_abs * (a.scale ? *a.scale : 1.0));
 
-  // the original diagonal: pivot j is dropped when its Schur complement is at most
-  // thr_rel * K_jj (the rounding noise of the FP32 Gram and of the elimination)
-  for (int i = tid; i < nb * QB; i += QBT) s_kd[i] = i < n ? K[i + (int64_t)i * ldk] : 0.f;
-  // owned lower blocks; a diagonal block as its full symmetric square read from the
-  // lower triangle; entries past n are zero (their pivots are dropped)
-  for (int e = tid; e < S * S * 1024; e += QBT) {
-    const int sl = e >> 10, w = e & 1023, a = sl / S, b = sl % S;
-    const int i = 4 * a + pr, j = 4 * b + pc;
-    const int c = w >> 5, r = w & 31;  // consecutive threads: consecutive rows (coalesced reads)
-    const int row = QB * i + r, col = QB * j + c;
-    float v = 0.f;
-    if (i < nb && j <= i && row < n && col < n)
-      v = row >= col ? K[row + (int64_t)col * ldk] : K[col + (int64_t)row * ldk];
-    slots[(size_t)sl * 1024 + qsw(r, c)] = v;
+  bool near = false;
+  if (RM) {
+    if (tid == 0) s_flag[0] = a.near_tol > 0.0 ? 1 : 0;
+    __syncthreads();
+    if (a.near_tol > 0.0) {
+      // |g| <= tol off the diagonal, |g - 1| <= tol on it (NaN fails), on the FP64 Gram
+      bool ok = true;
+      for (int e = tid; e < S * S * 1024; e += QBT) {
+        const int sl = e >> 10, w = e & 1023, ia = sl / S, ib = sl % S;
+        const int i = 4 * ia + pr, j = 4 * ib + pc;
+        const int row = QB * i + (w >> 5), col = QB * j + (w & 31);
+        if (i >= nb || j > i || row >= n || col >= n || row < col) continue;
+        const double g = (double)K[row + ldk * col];
+        ok = ok && (row == col ? fabs(g - 1.0) <= a.near_tol : fabs(g) <= a.near_tol);
+      }
+      if (!ok) s_flag[0] = 0;  // benign race: every writer stores 0
+    }
+    cluster.sync();
+    if (tid == 0) {
+      int all = 1;
+      for (int q = 0; q < 16; ++q) all &= *cluster.map_shared_rank(&s_flag[0], q);
+      s_flag[1] = all;
+    }
+    __syncthreads();
+    near = s_flag[1] != 0;
+    if (a.near_out != nullptr && rank == 0 && tid == 0) *a.near_out = near ? 1 : 0;
   }
-  __syncthreads();
 
-  for (int k = 0; k < nb; ++k) {
+  if (!near) {
+    // the original diagonal, for the relative drop threshold
+    for (int i = tid; i < nb * QB; i += QBT) s_kd[i] = i < n ? (float)K[i + ldk * i] : 0.f;
+    // owned lower blocks; a diagonal block as its full symmetric square read from the
+    // lower triangle; entries past n are zero (their pivots are dropped)
+    for (int e = tid; e < S * S * 1024; e += QBT) {
+      const int sl = e >> 10, w = e & 1023, ia = sl / S, ib = sl % S;
+      const int i = 4 * ia + pr, j = 4 * ib + pc;
+      const int c = w >> 5, r = w & 31;  // consecutive threads: consecutive rows (coalesced reads)
+      const int row = QB * i + r, col = QB * j + c;
+      float v = 0.f;
+      if (i < nb && j <= i && row < n && col < n)
+        v = (float)(row >= col ? K[row + ldk * col] : K[col + ldk * row]);
+      slots[(size_t)sl * 1024 + qsw(r, c)] = v;
+    }
+    __syncthreads();
+  }
+
+  for (int k = 0; k < (near ? 0 : nb); ++k) {
     const int dk = k & 3, kb = k >> 2;
     // ---- A: factor the diagonal block; lane r keeps row r (read as column r of the
     // symmetric square), pivots and the current column broadcast by shuffles
     if (pr == dk && pc == dk && wid == 0) {
       float* D = slot(kb, kb);
-      const float thr = thr_rel * s_kd[k * QB + lane];
+      const float thr = fmaxf(a.thr_rel * s_kd[k * QB + lane], thr_abs);
       float d[QB];
 #pragma unroll
       for (int c = 0; c < QB; ++c) d[c] = D[qsw(c, lane)];
@@ -477,9 +520,9 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const float* __restrict_
       if (tid < 32) inv_local[tid] = rI[tid];
       __syncthreads();
       for (int t = tid; t < S * QB; t += QBT) {
-        const int a = t >> 5, r = t & 31, i = 4 * a + pr;
+        const int ia = t >> 5, r = t & 31, i = 4 * ia + pr;
         if (i <= k || i >= nb) continue;
-        float* B = slot(a, kb) + r * QB;
+        float* B = slot(ia, kb) + r * QB;
         float x[QB];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -514,13 +557,13 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const float* __restrict_
     {
       const int rsrc = pr * 4 + dk, csrc = pc * 4 + dk;
       for (int e = tid; e < 2 * S * 256; e += QBT) {
-        const int half = e / (S * 256), w = e % (S * 256), a = w >> 8, o = w & 255;
-        const int g = 4 * a + (half ? pc : pr);
+        const int half = e / (S * 256), w = e % (S * 256), ia = w >> 8, o = w & 255;
+        const int g = 4 * ia + (half ? pc : pr);
         if (g <= k || g >= nb) continue;
         const int r = o & 31, q = o >> 5;
-        const float4* src = (const float4*)cluster.map_shared_rank(slot(a, kb), half ? csrc : rsrc);
+        const float4* src = (const float4*)cluster.map_shared_rank(slot(ia, kb), half ? csrc : rsrc);
         const float4 v = src[(r * QB + (((q ^ r) & 7) << 2)) >> 2];
-        float* dst = (half ? LjT : LiT) + (size_t)a * 1024 + r;
+        float* dst = (half ? LjT : LiT) + (size_t)ia * 1024 + r;
         dst[(4 * q + 0) * QB] = v.x;
         dst[(4 * q + 1) * QB] = v.y;
         dst[(4 * q + 2) * QB] = v.z;
@@ -529,12 +572,12 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const float* __restrict_
       __syncthreads();
       // 4 x 4 tiles, 64 per block (a warp covers half a block: uniform branches)
       for (int e = tid; e < S * S * 64; e += QBT) {
-        const int sl = e >> 6, t = e & 63, a = sl / S, b = sl % S;
-        const int i = 4 * a + pr, j = 4 * b + pc;
+        const int sl = e >> 6, t = e & 63, ia = sl / S, ib = sl % S;
+        const int i = 4 * ia + pr, j = 4 * ib + pc;
         if (j <= k || j > i || i >= nb) continue;
         const int r0 = (t >> 3) << 2, c0 = (t & 7) << 2;
-        const float* li = LiT + (size_t)a * 1024 + r0;
-        const float* lj = LjT + (size_t)b * 1024 + c0;
+        const float* li = LiT + (size_t)ia * 1024 + r0;
+        const float* lj = LjT + (size_t)ib * 1024 + c0;
         float acc[4][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -554,52 +597,80 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const float* __restrict_
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int row = r0 + u;
-          float4* p = (float4*)(T + row * QB + ((((c0 >> 2) ^ row) & 7) << 2));
-          float4 o = *p;
+          float4* pp = (float4*)(T + row * QB + ((((c0 >> 2) ^ row) & 7) << 2));
+          float4 o = *pp;
           o.x -= acc[u][0];
           o.y -= acc[u][1];
           o.z -= acc[u][2];
           o.w -= acc[u][3];
-          *p = o;
+          *pp = o;
         }
       }
       __syncthreads();
     }
   }
-  // ---- output: W = G, column-major rows_pad x cols_pad; a warp per column of this
-  // CTA's block columns, lanes over the rows of its block rows
-  const int nrb = rows_pad / QB;
-  for (int u = wid; u < Sc * QB; u += QBT / 32) {
-    const int b = u >> 5, c = u & 31, jb = 4 * b + pc, col = jb * QB + c;
-    double ss = 0.0;
-    if (col < cols_pad) {
-      for (int ib = pr; ib < nrb; ib += 4) {
-        float v = 0.f;
-        if (ib < nb && jb <= ib) {
-          const float* blk = slot(ib >> 2, b);
-          v = ib != jb ? blk[qsw(lane, c)] : (lane >= c ? blk[qsw(c, lane)] : 0.f);
-        }
-        W[ib * QB + lane + (int64_t)col * rows_pad] = v;
-        ss += (double)v * (double)v;
+
+  if (RM) {
+    // R = G^T (n x n, column-major, FP64): the owner of lower block (bi, bj) writes
+    // R(col, row) = G(row, col) for row >= col and the zero R(row, col) for row > col,
+    // so every entry of R is written once; near identity: R = I + Phi(E) from the
+    // FP64 Gram (strict upper part of E = G - I plus half its diagonal)
+    double* R = a.R;
+    for (int e = tid; e < S * S * 1024; e += QBT) {
+      const int sl = e >> 10, w = e & 1023, ia = sl / S, ib = sl % S;
+      const int bi = 4 * ia + pr, bj = 4 * ib + pc;
+      if (bi >= nb || bj > bi) continue;
+      const int r = w >> 5, c = w & 31;  // consecutive threads: consecutive columns of R
+      const int row = QB * bi + r, col = QB * bj + c;
+      if (row >= n || col >= n || row < col) continue;
+      double v;
+      if (near) {
+        const double g = (double)K[row + ldk * col];
+        v = row == col ? 1.0 + 0.5 * (g - 1.0) : g;
+      } else {
+        v = (double)(bi != bj ? slots[(size_t)sl * 1024 + qsw(r, c)] : slots[(size_t)sl * 1024 + qsw(c, r)]);
       }
+      R[col + (int64_t)row * n] = v;
+      if (row > col) R[row + (int64_t)col * n] = 0.0;
     }
+  } else {
+    // W = G, column-major rows_pad x cols_pad; a warp per column of this CTA's
+    // block columns, lanes over the rows of its block rows
+    float* W = a.W;
+    const int nrb = rows_pad / QB;
+    for (int u = wid; u < Sc * QB; u += QBT / 32) {
+      const int ib = u >> 5, c = u & 31, jb = 4 * ib + pc, col = jb * QB + c;
+      double ss = 0.0;
+      if (col < cols_pad) {
+        for (int rb = pr; rb < nrb; rb += 4) {
+          float v = 0.f;
+          if (rb < nb && jb <= rb) {
+            const float* blk = slot(rb >> 2, ib);
+            v = rb != jb ? blk[qsw(lane, c)] : (lane >= c ? blk[qsw(c, lane)] : 0.f);
+          }
+          W[rb * QB + lane + (int64_t)col * rows_pad] = v;
+          ss += (double)v * (double)v;
+        }
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) colpart[u] = ss;
-  }
-  cluster.sync();
-  if (pr == 0) {
-    for (int u = tid; u < Sc * QB; u += QBT) {
-      const int col = (4 * (u >> 5) + pc) * QB + (u & 31);
-      if (col >= cols_pad) continue;
-      double t = 0.0;
-      for (int q = 0; q < 4; ++q) t += *cluster.map_shared_rank(colpart + u, q * 4 + pc);
-      colnorm2[col] = t;
-      if (!isfinite(t)) report(BKFAC_ENONFINITE);
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      if (lane == 0) colpart[u] = ss;
+    }
+    cluster.sync();
+    if (pr == 0) {
+      for (int u = tid; u < Sc * QB; u += QBT) {
+        const int col = (4 * (u >> 5) + pc) * QB + (u & 31);
+        if (col >= cols_pad) continue;
+        double t = 0.0;
+        for (int q = 0; q < 4; ++q) t += *cluster.map_shared_rank(colpart + u, q * 4 + pc);
+        a.colnorm2[col] = t;
+        if (!isfinite(t)) report(BKFAC_ENONFINITE);
+      }
     }
   }
   cluster.sync();  // keep shared memory alive until every remote read is done
 }
+
 }  // namespace
 
 // blocked cluster Cholesky: n x n with n <= 576 (at most 9 x 9 blocks per CTA)
@@ -650,21 +721,22 @@ bool chol_core_ok(int n, int rows_pad, int cols_pad) {
          chol_core_smem(n, cols_pad) <= 200 * 1024;
 }
 
-int launch_chol_core(const float* K, int ldk, int n, float* W, int rows_pad, int cols_pad, double* colnorm2,
-                     float thr_rel, cudaStream_t s) {
-  if (!chol_core_ok(n, rows_pad, cols_pad) || ldk < n) return (int)cudaErrorInvalidValue;
+namespace {
+template <typename TK, bool RM>
+int launch_core_typed(const CoreCholArgs& a, cudaStream_t s) {
   static std::atomic<int> configured{0};  // attributes set once (the call can stall the host)
   if (!configured.load()) {
-    cudaError_t e = cudaFuncSetAttribute(chol_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e =
+        cudaFuncSetAttribute(chol_core_kernel<TK, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(chol_core_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(chol_core_kernel<TK, RM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return (int)e;
     configured.store(1);
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(16, 1, 1);
   cfg.blockDim = dim3(QBT, 1, 1);
-  cfg.dynamicSmemBytes = chol_core_smem(n, cols_pad);
+  cfg.dynamicSmemBytes = chol_core_smem(a.n, a.cols_pad);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -673,10 +745,45 @@ int launch_chol_core(const float* K, int ldk, int n, float* W, int rows_pad, int
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const cudaError_t e =
-      cudaLaunchKernelEx(&cfg, chol_core_kernel, K, ldk, n, W, rows_pad, cols_pad, colnorm2, thr_rel);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, chol_core_kernel<TK, RM>, a);
   note_launches(1);
   return (int)e;
+}
+}  // namespace
+
+int launch_chol_core(const float* K, int ldk, int n, float* W, int rows_pad, int cols_pad, double* colnorm2,
+                     float thr_rel, cudaStream_t s) {
+  if (!chol_core_ok(n, rows_pad, cols_pad) || ldk < n) return (int)cudaErrorInvalidValue;
+  CoreCholArgs a{};
+  a.K = K;
+  a.ldk = ldk;
+  a.n = n;
+  a.thr_rel = thr_rel;
+  a.W = W;
+  a.rows_pad = rows_pad;
+  a.cols_pad = cols_pad;
+  a.colnorm2 = colnorm2;
+  return launch_core_typed<float, false>(a, s);
+}
+
+bool chol_r32_ok(int n) { return n >= 1 && chol_core_ok(n, (int)round_up(n, QB), n); }
+
+int launch_chol_r32(const double* Gm, int n, double* R, float thr_rel, double thr_abs, const double* scale,
+                    double near_tol, int* near_out, cudaStream_t s) {
+  if (!chol_r32_ok(n)) return (int)cudaErrorInvalidValue;
+  CoreCholArgs a{};
+  a.K = Gm;
+  a.ldk = n;
+  a.n = n;
+  a.thr_rel = thr_rel;
+  a.thr_abs = thr_abs;
+  a.scale = scale;
+  a.R = R;
+  a.rows_pad = (int)round_up(n, QB);
+  a.cols_pad = n;
+  a.near_tol = near_tol;
+  a.near_out = near_out;
+  return launch_core_typed<double, true>(a, s);
 }
 
 // cluster size for an n x n factorisation (two n x w FP64 buffers per CTA)

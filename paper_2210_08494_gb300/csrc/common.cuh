@@ -131,9 +131,29 @@ int launch_chol_block(const double* Gm, int n, double* R, double thr_rel, const 
 // column-major rows_pad x cols_pad matrix G (zero above the diagonal and beyond n)
 // with its columns' squared norms; pivot j is dropped (zero column of G) when its
 // Schur complement is <= thr_rel * K_jj; for n <= 768 (chol_core_ok)
+struct CoreCholArgs {
+  const void* K;  // n x n symmetric (lower triangle read), column-major: float (W mode) or double (R mode)
+  int64_t ldk;
+  int n;
+  float thr_rel;        // drop pivot j when its Schur complement <= max(thr_rel K_jj, thr_abs * scale)
+  double thr_abs;
+  const double* scale;  // may be null (= 1)
+  float* W;             // W mode: G, column-major rows_pad x cols_pad
+  int rows_pad, cols_pad;
+  double* colnorm2;     // W mode: squared column norms (cols_pad)
+  double* R;            // R mode: G^T, n x n column-major FP64
+  double near_tol;      // R mode: near-identity shortcut when > 0
+  int* near_out;        // R mode: 1 when the shortcut was taken (may be null)
+};
 bool chol_core_ok(int n, int rows_pad, int cols_pad);
 int launch_chol_core(const float* K, int ldk, int n, float* W, int rows_pad, int cols_pad, double* colnorm2,
                      float thr_rel, cudaStream_t s);
+// the same FP32 factorisation of an FP64 Gram (CholeskyQR of the FP32 and mixed
+// paths): R = G^T as n x n column-major FP64, with the near-identity shortcut of
+// launch_chol_cluster when near_tol > 0; for n <= 768
+bool chol_r32_ok(int n);
+int launch_chol_r32(const double* Gm, int n, double* R, float thr_rel, double thr_abs, const double* scale,
+                    double near_tol, int* near_out, cudaStream_t s);
 // inverse of the upper-triangular R (zero rows = dropped pivots -> zero rows/cols of Rinv);
 // when near (may be null) points to a nonzero flag, R = I + F is near identity and
 // Rinv = I - F (exact to O(|F|^2)) is written instead

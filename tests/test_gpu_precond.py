@@ -124,3 +124,32 @@ def test_preconditioned_trajectory_stays_close(oracle):
     U2, s2 = gpu_state(f)
     assert rel(s2, so) < 1e-3
     assert lowrank_rel_err(U2, s2, Uo, so) < 1e-3
+
+
+@pytest.mark.parametrize("eps", [1e-5, 3e-3])
+def test_fp32_choleskyqr_nearly_dependent_columns(oracle, eps):
+    """Batch columns that repeat others up to a relative perturbation eps: the residual
+    is ill-conditioned (kappa ~ 1/eps).  The FP32 and mixed paths factor its FP64 Gram
+    in FP32: at eps = 1e-5 the repeated directions fall below the FP32 elimination's
+    noise and are dropped (their energy, ~eps^2 of a column's, is far below the
+    tolerance); at eps = 3e-3 they are kept and the second CholeskyQR pass restores
+    orthonormality."""
+    d, r, n = 900, 96, 64
+    f = bkfac.Factor(d, r, bkfac.F32)
+    X0 = synth.powerlaw_batch(d, 2 * r, 1.2, 21, 0)
+    bkfac.bkfac_init(f, to_dev(X0, f))
+    check_status()
+    Ug, sg = gpu_state(f)
+    X = synth.powerlaw_batch(d, n, 1.2, 21, 1)
+    rng = np.random.default_rng(21)
+    for j in range(40, n):
+        src = X[j - 40]
+        X[j] = src + eps * np.linalg.norm(src) * rng.standard_normal(d) / np.sqrt(d)
+    bkfac.bkfac_update(f, to_dev(X, f), 0.95)
+    check_status()
+    Uo, so, info = oracle.update(Ug, sg, Ug.shape[0], rounded(X, f), 0.95, r)
+    U2, s2 = gpu_state(f)
+    k = f.r_cur
+    assert rel(s2, so[:k]) < 1e-4
+    assert lowrank_rel_err(U2, s2, Uo[:k], so[:k]) < 1e-4
+    assert orth_err(U2[s2 > 0]) < orth_bound(r + n, 1)
