@@ -264,25 +264,40 @@ __global__ void __launch_bounds__(1024) trinv_blocked_kernel(const double* __res
 template <typename TM, typename J>
 __global__ void __launch_bounds__(256) assemble_core_kernel(const CoreArgs a) {
   __shared__ double red[32];
+  __shared__ J s_r1[1024];  // column jj of R1 (n <= 1024)
   const int j = blockIdx.x;
   J* col = (J*)a.L + (int64_t)j * a.rows_pad;
   const double sc = sqrt(a.c);
+  const int jj = j - a.k;
+  if (j >= a.k && j < a.N)
+    for (int l = threadIdx.x; l <= jj; l += blockDim.x) s_r1[l] = (J)a.R1[l + (int64_t)jj * a.n];
+  __syncthreads();
   double ss = 0.0;
   for (int i = threadIdx.x; i < a.rows_pad; i += blockDim.x) {
     double v = 0.0;
     if (j < a.k) {
       if (i == j) v = sqrt(a.rho * a.sigma[j]);
     } else if (j < a.N && i < a.N) {
-      const int jj = j - a.k;
       if (i < a.k) {
         v = sc * (double)((const TM*)a.M)[i + (int64_t)jj * a.ldm];
       } else {
         const int ii = i - a.k;
         if (ii <= jj) {
-          // (R2 R1)[ii, jj] = sum_{l = ii..jj} R2[ii, l] R1[l, jj]; accumulate in the Jacobi type
-          J s = J(0);
-          for (int l = ii; l <= jj; ++l) s += (J)a.R2[ii + (int64_t)l * a.n] * (J)a.R1[l + (int64_t)jj * a.n];
-          v = sc * (double)s;
+          // (R2 R1)[ii, jj] = sum_{l = ii..jj} R2[ii, l] R1[l, jj]; accumulate in the Jacobi
+          // type, four partial sums so that four loads of R2 are in flight
+          J s0 = J(0), s1 = J(0), s2 = J(0), s3 = J(0);
+          const double* r2 = a.R2 + ii;
+          int l = ii;
+          for (; l + 3 <= jj; l += 4) {
+            const J x0 = (J)r2[(int64_t)l * a.n], x1 = (J)r2[(int64_t)(l + 1) * a.n];
+            const J x2 = (J)r2[(int64_t)(l + 2) * a.n], x3 = (J)r2[(int64_t)(l + 3) * a.n];
+            s0 += x0 * s_r1[l];
+            s1 += x1 * s_r1[l + 1];
+            s2 += x2 * s_r1[l + 2];
+            s3 += x3 * s_r1[l + 3];
+          }
+          for (; l <= jj; ++l) s0 += (J)r2[(int64_t)l * a.n] * s_r1[l];
+          v = sc * (double)((s0 + s1) + (s2 + s3));
         }
       }
     }
@@ -370,15 +385,17 @@ __global__ void __launch_bounds__(1024) sort_output_kernel(const SortArgs a) {
   }
   for (int i = wid; i < a.cols; i += nw) {
     const J* w = W + (int64_t)i * a.rows_pad;
-    J s0 = J(0), s1 = J(0);
+    J s0 = J(0), s1 = J(0), s2 = J(0), s3 = J(0);  // four loads in flight per lane
     int r = lane;
-    for (; r + 32 < a.rows; r += 64) {
-      const J v0 = w[r], v1 = w[r + 32];
+    for (; r + 96 < a.rows; r += 128) {
+      const J v0 = w[r], v1 = w[r + 32], v2 = w[r + 64], v3 = w[r + 96];
       s0 += v0 * v0;
       s1 += v1 * v1;
+      s2 += v2 * v2;
+      s3 += v3 * v3;
     }
-    if (r < a.rows) s0 += w[r] * w[r];
-    J sum = s0 + s1;
+    for (; r < a.rows; r += 32) s0 += w[r] * w[r];
+    J sum = (s0 + s1) + (s2 + s3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) lam[i] = sum;
@@ -408,6 +425,7 @@ __global__ void __launch_bounds__(1024) sort_output_kernel(const SortArgs a) {
     const J sc = li > tiny ? J(1) / sqrt(li) : J(0);
     const J* w = W + (int64_t)i * a.rows_pad;
     TO* v = (TO*)a.V + (int64_t)rk * a.ldv;
+#pragma unroll 4
     for (int r = lane; r < a.rows; r += 32) v[r] = (TO)(w[r] * sc);
   }
 }
