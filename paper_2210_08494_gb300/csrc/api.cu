@@ -120,7 +120,7 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
     cols_cap = (int)round_up(f->r + n, 32) + 128;
     p.o_L = L.add((size_t)rows_cap * cols_cap * jes);
     p.o_cn = L.add((size_t)cols_cap * 8);
-    p.o_lam = L.add((size_t)cols_cap * 8);
+    p.o_lam = L.add((size_t)cols_cap * 16);  // eigenvalues + the sort's scratch
     p.o_sw = L.add(256);
     p.o_st = L.add((size_t)cols_cap * 4);
   } else {
@@ -150,7 +150,7 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
     p.o_Rinv = L.add((size_t)n * n * es);
     p.o_L = L.add((size_t)rows_cap * cols_cap * jes);
     p.o_cn = L.add((size_t)cols_cap * 8);
-    p.o_lam = L.add((size_t)cols_cap * 8);
+    p.o_lam = L.add((size_t)cols_cap * 16);  // eigenvalues + the sort's scratch
     p.o_V = L.add((size_t)p.ldv * r_total(f) * es);
     p.o_Un = L.add((size_t)p.ldq * r_total(f) * es);
     p.o_sw = L.add(256);
@@ -196,7 +196,7 @@ ReorthPlan plan_reorth(const bkfac_factor* f, int k) {
   p.o_Q = L.add((size_t)p.ldq * kmax * es);
   p.o_L = L.add((size_t)p.rows_cap * p.cols_cap * jes);
   p.o_cn = L.add((size_t)p.cols_cap * 8);
-  p.o_lam = L.add((size_t)p.cols_cap * 8);
+  p.o_lam = L.add((size_t)p.cols_cap * 16);  // eigenvalues + the sort's scratch
   p.o_V = L.add((size_t)p.ldv * kmax * es);
   p.o_Un = L.add((size_t)p.ldq * kmax * es);
   p.o_sw = L.add(256);
@@ -670,7 +670,7 @@ SmallEvd plan_small_evd(int n, const Prec& pr, Layout& L) {
   e.o_scale = L.add(8);
   e.o_L = L.add((size_t)e.rows_pad * e.cols_pad * jes);
   e.o_cn = L.add((size_t)e.cols_pad * 8);
-  e.o_lams = L.add((size_t)e.cols_pad * 8);
+  e.o_lams = L.add((size_t)e.cols_pad * 16);  // eigenvalues + the sort's scratch
   e.o_V = L.add((size_t)e.ldv * n * es);
   e.o_lam = L.add((size_t)std::max(n, 1) * 8);
   e.o_sw = L.add(256);

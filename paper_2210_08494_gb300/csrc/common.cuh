@@ -238,7 +238,7 @@ struct SortArgs {
   int64_t ldv;
   double* sig;           // r_sig values written (rank < r_out), zero-filled up to r_sig
   int r_sig;
-  double* lam_sorted;    // optional, cols values
+  double* lam_sorted;    // 2 cols values: the sorted eigenvalues, then scratch for the sort
   const double* colnorm2; // cols_pad squared column norms of the Jacobi input
   int cols_pad;
 };

@@ -365,17 +365,43 @@ __global__ void __launch_bounds__(256) assemble_reorth_kernel(const double* R, c
 // lambda_i = ||w_i||^2 (the eigenvalues of W W^T), eigenvectors w_i / ||w_i||,
 // ordered descending with ties broken by column index; the first r_out go to
 // (V, sig).  Columns whose norm is at the rounding level of the input (relative
-// to ||W||_F^2) are returned as zero vectors with sigma = 0.
+// to ||W||_F^2) are returned as zero vectors with sigma = 0.  Norms, ordering and
+// scaling are in the Jacobi type J (FP32 arithmetic for the FP32 paths); only the
+// eigenvalues handed back are widened to double.  Two kernels over many blocks (a
+// warp per column), so that the loads of W overlap across the GPU.
+
+// squared column norms (the J value, stored as double), four loads in flight per lane
+template <typename J>
+__global__ void __launch_bounds__(256) col_sumsq_kernel(const J* __restrict__ W, int rows, int rows_pad, int cols,
+                                                        double* out) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= cols) return;
+  const J* w = W + (int64_t)i * rows_pad;
+  J s0 = J(0), s1 = J(0), s2 = J(0), s3 = J(0);
+  int r = lane;
+  for (; r + 96 < rows; r += 128) {
+    const J v0 = w[r], v1 = w[r + 32], v2 = w[r + 64], v3 = w[r + 96];
+    s0 += v0 * v0;
+    s1 += v1 * v1;
+    s2 += v2 * v2;
+    s3 += v3 * v3;
+  }
+  for (; r < rows; r += 32) s0 += w[r] * w[r];
+  J sum = (s0 + s1) + (s2 + s3);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) out[i] = (double)sum;
+}
+
+// rank of each column (a warp per column, lanes over the others) and the output
 template <typename J, typename TO>
-__global__ void __launch_bounds__(1024) sort_output_kernel(const SortArgs a) {
-  // norms, ordering and scaling in the Jacobi type J (FP32 arithmetic for the FP32
-  // paths); only the eigenvalues handed back are widened to double
+__global__ void __launch_bounds__(256) sort_write_kernel(const SortArgs a, const double* __restrict__ norms) {
   extern __shared__ __align__(16) unsigned char so_smem[];
   J* lam = (J*)so_smem;  // cols
-  int* rank = (int*)(lam + a.cols);
   __shared__ double s_tiny;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const J* W = (const J*)a.W;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = threadIdx.x; j < a.cols; j += blockDim.x) lam[j] = (J)norms[j];
   if (wid == 0) {
     // deterministic: fixed lane assignment, fixed shuffle tree
     double f = 0.0;
@@ -383,51 +409,31 @@ __global__ void __launch_bounds__(1024) sort_output_kernel(const SortArgs a) {
     f = warp_sum(f);
     if (lane == 0) s_tiny = 16.0 * Eps<J>::u * Eps<J>::u * f;
   }
-  for (int i = wid; i < a.cols; i += nw) {
-    const J* w = W + (int64_t)i * a.rows_pad;
-    J s0 = J(0), s1 = J(0), s2 = J(0), s3 = J(0);  // four loads in flight per lane
-    int r = lane;
-    for (; r + 96 < a.rows; r += 128) {
-      const J v0 = w[r], v1 = w[r + 32], v2 = w[r + 64], v3 = w[r + 96];
-      s0 += v0 * v0;
-      s1 += v1 * v1;
-      s2 += v2 * v2;
-      s3 += v3 * v3;
-    }
-    for (; r < a.rows; r += 32) s0 += w[r] * w[r];
-    J sum = (s0 + s1) + (s2 + s3);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) lam[i] = sum;
-  }
   __syncthreads();
+  if (blockIdx.x == 0 && a.sig)
+    for (int j = a.r_out + threadIdx.x; j < a.r_sig; j += blockDim.x) a.sig[j] = 0.0;
+  const int i = blockIdx.x * 8 + wid;
+  if (i >= a.cols) return;
   const J tiny = (J)s_tiny;
-  for (int i = threadIdx.x; i < a.cols; i += blockDim.x) {
-    const J li = lam[i];
-    int rk = 0;
-    for (int j = 0; j < a.cols; ++j) {
-      const J lj = lam[j];
-      rk += (lj > li) || (lj == li && j < i);
-    }
-    rank[i] = rk;
+  const J li = lam[i];
+  int rk = 0;
+  for (int j = lane; j < a.cols; j += 32) {
+    const J lj = lam[j];
+    rk += (lj > li) || (lj == li && j < i);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rk += __shfl_xor_sync(0xffffffffu, rk, o);
+  if (lane == 0) {
     if (!isfinite(li)) report(BKFAC_ENONFINITE);
     if (a.lam_sorted) a.lam_sorted[rk] = (double)li;
     if (rk < a.r_out && a.sig) a.sig[rk] = li > tiny ? (double)li : 0.0;
   }
-  if (a.sig)
-    for (int j = a.r_out + threadIdx.x; j < a.r_sig; j += blockDim.x) a.sig[j] = 0.0;
-  __syncthreads();
-  // write the selected columns, one warp per column
-  for (int i = wid; i < a.cols; i += nw) {
-    const int rk = rank[i];
-    if (rk >= a.r_out) continue;
-    const J li = lam[i];
-    const J sc = li > tiny ? J(1) / sqrt(li) : J(0);
-    const J* w = W + (int64_t)i * a.rows_pad;
-    TO* v = (TO*)a.V + (int64_t)rk * a.ldv;
+  if (rk >= a.r_out) return;
+  const J sc = li > tiny ? J(1) / sqrt(li) : J(0);
+  const J* w = (const J*)a.W + (int64_t)i * a.rows_pad;
+  TO* v = (TO*)a.V + (int64_t)rk * a.ldv;
 #pragma unroll 4
-    for (int r = lane; r < a.rows; r += 32) v[r] = (TO)(w[r] * sc);
-  }
+  for (int r = lane; r < a.rows; r += 32) v[r] = (TO)(w[r] * sc);
 }
 
 // ---------------------------------------------------------------- finalize
@@ -663,27 +669,25 @@ int launch_assemble_reorth(const double* R, const double* sigma, int k, int rows
 }
 
 template <typename J, typename TO>
-void sort_launch(const SortArgs& a, size_t smem, cudaStream_t s) {
-  static std::atomic<int> configured{0};  // attribute set once (the call can stall the host)
-  if (!configured.load()) {
-    cudaFuncSetAttribute(sort_output_kernel<J, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    configured.store(1);
-  }
-  sort_output_kernel<J, TO><<<1, 1024, smem, s>>>(a);
+void sort_launch(const SortArgs& a, double* norms, cudaStream_t s) {
+  const unsigned blocks = (unsigned)ceil_div(a.cols, 8);
+  col_sumsq_kernel<J><<<blocks, 256, 0, s>>>((const J*)a.W, a.rows, a.rows_pad, a.cols, norms);
+  sort_write_kernel<J, TO><<<blocks, 256, (size_t)a.cols * sizeof(J), s>>>(a, norms);
 }
 
 int launch_sort_output(const SortArgs& a, DType j_t, DType out_t, cudaStream_t s) {
-  const size_t smem = (size_t)a.cols * (sizeof(double) + sizeof(int));  // bound for either J
-  if (smem > 200 * 1024) return (int)cudaErrorInvalidValue;
+  if (a.cols <= 0) return 0;
+  if ((size_t)a.cols * sizeof(double) > 48 * 1024 || a.lam_sorted == nullptr) return (int)cudaErrorInvalidValue;
+  double* norms = a.lam_sorted + a.cols;  // the second half of lam_sorted is scratch
   if (j_t == DT_F64 && out_t == DT_F64)
-    sort_launch<double, double>(a, smem, s);
+    sort_launch<double, double>(a, norms, s);
   else if (j_t == DT_F32 && out_t == DT_F32)
-    sort_launch<float, float>(a, smem, s);
+    sort_launch<float, float>(a, norms, s);
   else if (j_t == DT_F64 && out_t == DT_F32)
-    sort_launch<double, float>(a, smem, s);
+    sort_launch<double, float>(a, norms, s);
   else
-    sort_launch<float, double>(a, smem, s);
-  note_launches(1);
+    sort_launch<float, double>(a, norms, s);
+  note_launches(2);
   return (int)cudaGetLastError();
 }
 
