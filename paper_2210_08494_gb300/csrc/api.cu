@@ -550,7 +550,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     kg.b_kmaj = false;
     kg.C = Kc;
     kg.ldc = p.N;
-    kg.splits = gemm_pick_splits(p.N, p.N, p.N, 152);
+    kg.splits = std::max(1, std::min(8, p.N / 64));  // 16 output tiles at N = 512: split K to fill the GPU
     kg.partial = part;
     kg.partial_bytes = p.part_bytes;
     PHASE(PH_PRECOND, gemm_run(kg, DT_F32, DT_F32, DT_F32, s));

@@ -442,15 +442,18 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const CoreCholArgs a) {
     if (tid == 0) s_flag[0] = a.near_tol > 0.0 ? 1 : 0;
     __syncthreads();
     if (a.near_tol > 0.0) {
-      // |g| <= tol off the diagonal, |g - 1| <= tol on it (NaN fails), on the FP64 Gram
+      // |g| <= tol off the diagonal, 1 - tol <= g <= 1 + tol on it (NaN fails), on the
+      // FP64 Gram, as integer compares of the IEEE bit patterns (no FP64 arithmetic)
+      const long long tolb = __double_as_longlong(a.near_tol);
+      const long long lob = __double_as_longlong(1.0 - a.near_tol), hib = __double_as_longlong(1.0 + a.near_tol);
       bool ok = true;
       for (int e = tid; e < S * S * 1024; e += QBT) {
         const int sl = e >> 10, w = e & 1023, ia = sl / S, ib = sl % S;
         const int i = 4 * ia + pr, j = 4 * ib + pc;
-        const int row = QB * i + (w >> 5), col = QB * j + (w & 31);
+        const int row = QB * i + (w & 31), col = QB * j + (w >> 5);  // consecutive threads: consecutive rows
         if (i >= nb || j > i || row >= n || col >= n || row < col) continue;
-        const double g = (double)K[row + ldk * col];
-        ok = ok && (row == col ? fabs(g - 1.0) <= a.near_tol : fabs(g) <= a.near_tol);
+        const long long bits = __double_as_longlong((double)K[row + ldk * col]);
+        ok = ok && (row == col ? (bits >= lob && bits <= hib) : (bits & 0x7fffffffffffffffLL) <= tolb);
       }
       if (!ok) s_flag[0] = 0;  // benign race: every writer stores 0
     }
@@ -470,6 +473,7 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const CoreCholArgs a) {
     for (int i = tid; i < nb * QB; i += QBT) s_kd[i] = i < n ? (float)K[i + ldk * i] : 0.f;
     // owned lower blocks; a diagonal block as its full symmetric square read from the
     // lower triangle; entries past n are zero (their pivots are dropped)
+#pragma unroll 8
     for (int e = tid; e < S * S * 1024; e += QBT) {
       const int sl = e >> 10, w = e & 1023, ia = sl / S, ib = sl % S;
       const int i = 4 * ia + pr, j = 4 * ib + pc;
@@ -494,16 +498,25 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const CoreCholArgs a) {
 #pragma unroll
       for (int c = 0; c < QB; ++c) d[c] = D[qsw(c, lane)];
       bool bad = false;
+      // the pivot of column j + 1 is formed by every lane from two shuffles taken as soon
+      // as column j is scaled (the same fma that lane j + 1 applies to its own entry),
+      // so that the chain between pivots holds one shuffle, not two
+      float p = __shfl_sync(0xffffffffu, d[0], 0);
 #pragma unroll
       for (int j = 0; j < QB; ++j) {
-        const float p = __shfl_sync(0xffffffffu, d[j], j);
         bad |= !(fabsf(p) <= 3.402823466e38f);  // NaN or infinite
         const float il = p > __shfl_sync(0xffffffffu, thr, j) ? rsqrtf(p) : 0.f;
         const float l = lane >= j ? d[j] * il : 0.f;
         d[j] = l;
         if (lane == j) inv[j] = il;
+        if (j + 1 < QB) {
+          const float dn = __shfl_sync(0xffffffffu, d[(j + 1) % QB], (j + 1) % QB);
+          const float ln = __shfl_sync(0xffffffffu, l, (j + 1) % QB);
+          d[(j + 1) % QB] = fmaf(-l, ln, d[(j + 1) % QB]);
+          p = fmaf(-ln, ln, dn);
+        }
 #pragma unroll
-        for (int c = j + 1; c < QB; ++c) d[c] = fmaf(-l, __shfl_sync(0xffffffffu, l, c), d[c]);
+        for (int c = j + 2; c < QB; ++c) d[c] = fmaf(-l, __shfl_sync(0xffffffffu, l, c), d[c]);
       }
       if (bad && lane == 0) report(BKFAC_ENONFINITE);
       // element (c, r) of the stored block = L_kk[r][c] (zero for c > r)
@@ -556,18 +569,36 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const CoreCholArgs a) {
     // ---- C: trailing update of the owned blocks (i, j), k < j <= i
     {
       const int rsrc = pr * 4 + dk, csrc = pc * 4 + dk;
-      for (int e = tid; e < 2 * S * 256; e += QBT) {
+      // every remote load of this thread first (at most 2 S / 2 <= kCoreMaxN / 128 of them),
+      // then the local stores: the generic remote pointers could alias the local tiles,
+      // so interleaving them would serialise the loads
+      constexpr int kMaxCopy = kCoreMaxN / 128;
+      float4 cv[kMaxCopy];
+#pragma unroll
+      for (int u = 0; u < kMaxCopy; ++u) {
+        const int e = tid + u * QBT;
+        cv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e >= 2 * S * 256) continue;
         const int half = e / (S * 256), w = e % (S * 256), ia = w >> 8, o = w & 255;
         const int g = 4 * ia + (half ? pc : pr);
         if (g <= k || g >= nb) continue;
         const int r = o & 31, q = o >> 5;
         const float4* src = (const float4*)cluster.map_shared_rank(slot(ia, kb), half ? csrc : rsrc);
-        const float4 v = src[(r * QB + (((q ^ r) & 7) << 2)) >> 2];
+        cv[u] = src[(r * QB + (((q ^ r) & 7) << 2)) >> 2];
+      }
+#pragma unroll
+      for (int u = 0; u < kMaxCopy; ++u) {
+        const int e = tid + u * QBT;
+        if (e >= 2 * S * 256) continue;
+        const int half = e / (S * 256), w = e % (S * 256), ia = w >> 8, o = w & 255;
+        const int g = 4 * ia + (half ? pc : pr);
+        if (g <= k || g >= nb) continue;
+        const int r = o & 31, q = o >> 5;
         float* dst = (half ? LjT : LiT) + (size_t)ia * 1024 + r;
-        dst[(4 * q + 0) * QB] = v.x;
-        dst[(4 * q + 1) * QB] = v.y;
-        dst[(4 * q + 2) * QB] = v.z;
-        dst[(4 * q + 3) * QB] = v.w;
+        dst[(4 * q + 0) * QB] = cv[u].x;
+        dst[(4 * q + 1) * QB] = cv[u].y;
+        dst[(4 * q + 2) * QB] = cv[u].z;
+        dst[(4 * q + 3) * QB] = cv[u].w;
       }
       __syncthreads();
       // 4 x 4 tiles, 64 per block (a warp covers half a block: uniform branches)
@@ -638,9 +669,12 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const CoreCholArgs a) {
     // block columns, lanes over the rows of its block rows
     float* W = a.W;
     const int nrb = rows_pad / QB;
+    // (the sums are FP32: the Jacobi recomputes its norms from the columns at the start of
+    // every sweep and uses these only for its negligible-column threshold; FP64 arithmetic
+    // runs at 1/64 of the FP32 rate)
     for (int u = wid; u < Sc * QB; u += QBT / 32) {
       const int ib = u >> 5, c = u & 31, jb = 4 * ib + pc, col = jb * QB + c;
-      double ss = 0.0;
+      float ss = 0.f;
       if (col < cols_pad) {
         for (int rb = pr; rb < nrb; rb += 4) {
           float v = 0.f;
@@ -649,12 +683,12 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const CoreCholArgs a) {
             v = rb != jb ? blk[qsw(lane, c)] : (lane >= c ? blk[qsw(c, lane)] : 0.f);
           }
           W[rb * QB + lane + (int64_t)col * rows_pad] = v;
-          ss += (double)v * (double)v;
+          ss = fmaf(v, v, ss);
         }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-      if (lane == 0) colpart[u] = ss;
+      if (lane == 0) colpart[u] = (double)ss;
     }
     cluster.sync();
     if (pr == 0) {
