@@ -413,6 +413,88 @@ constexpr int kCoreMaxN = 768;   // 6 x 6 blocks per CTA: the most that fit in s
 
 __device__ __forceinline__ int qsw(int r, int c) { return r * QB + ((((c >> 2) ^ r) & 7) << 2) + (c & 3); }
 
+// Factor a 32 x 32 diagonal block in place, one warp: D holds the full symmetric
+// square (swizzled) and receives L_kk^T (element (c, r) = L_kk[r][c], zero for
+// c > r); inv[j] = 1 / L_kk[j][j] (0 for a dropped pivot).  Lane r keeps row r
+// (read as column r of the square).  The pivot of column j + 1 comes from two
+// shuffles taken as soon as column j is scaled (the same fma that lane j + 1
+// applies to its own entry), so the chain between pivots holds one shuffle; the
+// rest of column j reaches the lanes through shared memory (s_l, two 32-float
+// buffers) as 128-bit broadcasts.
+__device__ __forceinline__ void factor_diag_block(float* D, float* inv, float* s_l, float thr, int lane) {
+  float d[QB];
+#pragma unroll
+  for (int c = 0; c < QB; ++c) d[c] = D[qsw(c, lane)];
+  bool bad = false;
+  float p = __shfl_sync(0xffffffffu, d[0], 0);
+#pragma unroll
+  for (int j = 0; j < QB; ++j) {
+    bad |= !(fabsf(p) <= 3.402823466e38f);  // NaN or infinite
+    const float il = p > __shfl_sync(0xffffffffu, thr, j) ? rsqrtf(p) : 0.f;
+    const float l = lane >= j ? d[j] * il : 0.f;
+    d[j] = l;
+    if (lane == j) inv[j] = il;
+    if (j + 1 < QB) {
+      const float dn = __shfl_sync(0xffffffffu, d[(j + 1) % QB], (j + 1) % QB);
+      const float ln = __shfl_sync(0xffffffffu, l, (j + 1) % QB);
+      d[(j + 1) % QB] = fmaf(-l, ln, d[(j + 1) % QB]);
+      p = fmaf(-ln, ln, dn);
+    }
+    if (j + 2 < QB) {
+      // buffer j & 1 is rewritten two columns later, after every lane has passed the
+      // next column's __syncwarp (and so finished reading it)
+      float* sb = s_l + (j & 1) * QB;
+      sb[lane] = l;
+      __syncwarp();
+#pragma unroll
+      for (int q = (j + 2) >> 2; q < 8; ++q) {
+        const float4 v = *(const float4*)(sb + 4 * q);
+        if (4 * q + 0 >= j + 2) d[(4 * q + 0) % QB] = fmaf(-l, v.x, d[(4 * q + 0) % QB]);
+        if (4 * q + 1 >= j + 2) d[(4 * q + 1) % QB] = fmaf(-l, v.y, d[(4 * q + 1) % QB]);
+        if (4 * q + 2 >= j + 2) d[(4 * q + 2) % QB] = fmaf(-l, v.z, d[(4 * q + 2) % QB]);
+        if (4 * q + 3 >= j + 2) d[(4 * q + 3) % QB] = fmaf(-l, v.w, d[(4 * q + 3) % QB]);
+      }
+    }
+  }
+  if (bad && lane == 0) report(BKFAC_ENONFINITE);
+#pragma unroll
+  for (int c = 0; c < QB; ++c) D[qsw(c, lane)] = d[c];
+}
+
+// One 4 x 4 tile t (0..63) of a trailing block: T -= L_i L_j^T over the 32 columns of
+// the panel, from the transposed panel blocks li = L_i^T, lj = L_j^T ([m][row]).
+__device__ __forceinline__ void trail_tile(const float* li, const float* lj, float* T, int t) {
+  const int r0 = (t >> 3) << 2, c0 = (t & 7) << 2;
+  li += r0;
+  lj += c0;
+  float acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+#pragma unroll 8
+  for (int m = 0; m < QB; ++m) {
+    const float4 x = *(const float4*)(li + m * QB);
+    const float4 y = *(const float4*)(lj + m * QB);
+    const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xs[u], ys[v], acc[u][v]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int row = r0 + u;
+    float4* pp = (float4*)(T + row * QB + ((((c0 >> 2) ^ row) & 7) << 2));
+    float4 o = *pp;
+    o.x -= acc[u][0];
+    o.y -= acc[u][1];
+    o.z -= acc[u][2];
+    o.w -= acc[u][3];
+    *pp = o;
+  }
+}
+
 template <typename TK, bool RM>
 __global__ void __launch_bounds__(QBT) chol_core_kernel(const CoreCholArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -433,6 +515,7 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const CoreCholArgs a) {
   double* colpart = (double*)(inv_local + 32);  // this CTA's part of the columns' squared norms
   __shared__ float s_kd[kCoreMaxN];
   __shared__ int s_flag[2];  // near identity: [0] this CTA's blocks, [1] the cluster's decision
+  __shared__ __align__(16) float s_l[2 * QB];  // column broadcast buffers of factor_diag_block
   auto slot = [&](int ia, int ib) { return slots + (size_t)(ia * S + ib) * 1024; };
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const float thr_abs = (float)(a.thr_abs * (a.scale ? *a.scale : 1.0));
@@ -487,42 +570,24 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const CoreCholArgs a) {
     __syncthreads();
   }
 
+  // Panel blocks reach the trailing updates through global memory (L2) when the output
+  // buffer can hold them until the output phase (nb blocks of 1024 floats, transposed):
+  // one owner serving eight readers over distributed shared memory was the bottleneck.
+  // The output is written only after the last step, whose cluster barriers follow every
+  // read of the panel.
+  float* P = nullptr;
+  if (RM) {
+    if ((int64_t)2 * n * n >= (int64_t)nb * 1024) P = (float*)a.R;
+  } else {
+    if ((int64_t)rows_pad * cols_pad >= (int64_t)nb * 1024) P = a.W;
+  }
+  auto thr_of = [&](int k) { return fmaxf(a.thr_rel * s_kd[k * QB + lane], thr_abs); };
+
   for (int k = 0; k < (near ? 0 : nb); ++k) {
     const int dk = k & 3, kb = k >> 2;
-    // ---- A: factor the diagonal block; lane r keeps row r (read as column r of the
-    // symmetric square), pivots and the current column broadcast by shuffles
-    if (pr == dk && pc == dk && wid == 0) {
-      float* D = slot(kb, kb);
-      const float thr = fmaxf(a.thr_rel * s_kd[k * QB + lane], thr_abs);
-      float d[QB];
-#pragma unroll
-      for (int c = 0; c < QB; ++c) d[c] = D[qsw(c, lane)];
-      bool bad = false;
-      // the pivot of column j + 1 is formed by every lane from two shuffles taken as soon
-      // as column j is scaled (the same fma that lane j + 1 applies to its own entry),
-      // so that the chain between pivots holds one shuffle, not two
-      float p = __shfl_sync(0xffffffffu, d[0], 0);
-#pragma unroll
-      for (int j = 0; j < QB; ++j) {
-        bad |= !(fabsf(p) <= 3.402823466e38f);  // NaN or infinite
-        const float il = p > __shfl_sync(0xffffffffu, thr, j) ? rsqrtf(p) : 0.f;
-        const float l = lane >= j ? d[j] * il : 0.f;
-        d[j] = l;
-        if (lane == j) inv[j] = il;
-        if (j + 1 < QB) {
-          const float dn = __shfl_sync(0xffffffffu, d[(j + 1) % QB], (j + 1) % QB);
-          const float ln = __shfl_sync(0xffffffffu, l, (j + 1) % QB);
-          d[(j + 1) % QB] = fmaf(-l, ln, d[(j + 1) % QB]);
-          p = fmaf(-ln, ln, dn);
-        }
-#pragma unroll
-        for (int c = j + 2; c < QB; ++c) d[c] = fmaf(-l, __shfl_sync(0xffffffffu, l, c), d[c]);
-      }
-      if (bad && lane == 0) report(BKFAC_ENONFINITE);
-      // element (c, r) of the stored block = L_kk[r][c] (zero for c > r)
-#pragma unroll
-      for (int c = 0; c < QB; ++c) D[qsw(c, lane)] = d[c];
-    }
+    // ---- A: the first diagonal block; later ones are factored by their owner inside the
+    // previous step's trailing update (lookahead)
+    if (k == 0 && pr == 0 && pc == 0 && wid == 0) factor_diag_block(slot(0, 0), inv, s_l, thr_of(0), lane);
     cluster.sync();  // L_kk and its reciprocals are final
     // ---- B: the panel blocks below the diagonal, owned by the CTAs of grid column dk
     if (pc == dk) {
@@ -563,78 +628,99 @@ __global__ void __launch_bounds__(QBT) chol_core_kernel(const CoreCholArgs a) {
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           *(float4*)(B + (((q ^ r) & 7) << 2)) = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+        if (P != nullptr) {
+          // transposed into the panel buffer: element [m][r] of block i (coalesced over r)
+          float* pb = P + (size_t)i * 1024 + r;
+#pragma unroll
+          for (int m = 0; m < QB; ++m) pb[m * QB] = x[m];
+        }
       }
     }
-    cluster.sync();  // the panel of step k is final
+    cluster.sync();  // the panel of step k is final (in shared and in global memory)
     // ---- C: trailing update of the owned blocks (i, j), k < j <= i
     {
-      const int rsrc = pr * 4 + dk, csrc = pc * 4 + dk;
-      // every remote load of this thread first (at most 2 S / 2 <= kCoreMaxN / 128 of them),
-      // then the local stores: the generic remote pointers could alias the local tiles,
-      // so interleaving them would serialise the loads
-      constexpr int kMaxCopy = kCoreMaxN / 128;
-      float4 cv[kMaxCopy];
+      // transposed panel blocks (4a + pr, k) -> LiT[a] and (4b + pc, k) -> LjT[b]; a batch
+      // of loads first, then its stores: the generic remote pointers could alias the local
+      // tiles, so interleaving them would serialise the loads
+      constexpr int kMaxCopy = kCoreMaxN / 128;  // copies per thread at most (6 x 6 blocks)
+      constexpr int kBatch = 3;                  // loads in flight per batch
 #pragma unroll
-      for (int u = 0; u < kMaxCopy; ++u) {
-        const int e = tid + u * QBT;
-        cv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (e >= 2 * S * 256) continue;
-        const int half = e / (S * 256), w = e % (S * 256), ia = w >> 8, o = w & 255;
-        const int g = 4 * ia + (half ? pc : pr);
-        if (g <= k || g >= nb) continue;
-        const int r = o & 31, q = o >> 5;
-        const float4* src = (const float4*)cluster.map_shared_rank(slot(ia, kb), half ? csrc : rsrc);
-        cv[u] = src[(r * QB + (((q ^ r) & 7) << 2)) >> 2];
-      }
+      for (int u0 = 0; u0 < kMaxCopy; u0 += kBatch) {
+        float4 cv[kBatch];
+        if (P != nullptr) {
+          const float4* P4 = (const float4*)P;
 #pragma unroll
-      for (int u = 0; u < kMaxCopy; ++u) {
-        const int e = tid + u * QBT;
-        if (e >= 2 * S * 256) continue;
-        const int half = e / (S * 256), w = e % (S * 256), ia = w >> 8, o = w & 255;
-        const int g = 4 * ia + (half ? pc : pr);
-        if (g <= k || g >= nb) continue;
-        const int r = o & 31, q = o >> 5;
-        float* dst = (half ? LjT : LiT) + (size_t)ia * 1024 + r;
-        dst[(4 * q + 0) * QB] = cv[u].x;
-        dst[(4 * q + 1) * QB] = cv[u].y;
-        dst[(4 * q + 2) * QB] = cv[u].z;
-        dst[(4 * q + 3) * QB] = cv[u].w;
+          for (int u = 0; u < kBatch; ++u) {
+            const int e = tid + (u0 + u) * QBT;
+            cv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e >= 2 * S * 256) continue;
+            const int half = e / (S * 256), w = e % (S * 256), ia = w >> 8, o = w & 255;
+            const int g = 4 * ia + (half ? pc : pr);
+            if (g <= k || g >= nb) continue;
+            cv[u] = __ldcg(P4 + (size_t)g * 256 + o);  // L2 only: the buffer is rewritten every step
+          }
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int e = tid + (u0 + u) * QBT;
+            if (e >= 2 * S * 256) continue;
+            const int half = e / (S * 256), w = e % (S * 256), ia = w >> 8, o = w & 255;
+            const int g = 4 * ia + (half ? pc : pr);
+            if (g <= k || g >= nb) continue;
+            *(float4*)((half ? LjT : LiT) + (size_t)ia * 1024 + 4 * o) = cv[u];
+          }
+        } else {
+          const int rsrc = pr * 4 + dk, csrc = pc * 4 + dk;
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int e = tid + (u0 + u) * QBT;
+            cv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e >= 2 * S * 256) continue;
+            const int half = e / (S * 256), w = e % (S * 256), ia = w >> 8, o = w & 255;
+            const int g = 4 * ia + (half ? pc : pr);
+            if (g <= k || g >= nb) continue;
+            const int r = o & 31, q = o >> 5;
+            const float4* src = (const float4*)cluster.map_shared_rank(slot(ia, kb), half ? csrc : rsrc);
+            cv[u] = src[(r * QB + (((q ^ r) & 7) << 2)) >> 2];
+          }
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int e = tid + (u0 + u) * QBT;
+            if (e >= 2 * S * 256) continue;
+            const int half = e / (S * 256), w = e % (S * 256), ia = w >> 8, o = w & 255;
+            const int g = 4 * ia + (half ? pc : pr);
+            if (g <= k || g >= nb) continue;
+            const int r = o & 31, q = o >> 5;
+            float* dst = (half ? LjT : LiT) + (size_t)ia * 1024 + r;
+            dst[(4 * q + 0) * QB] = cv[u].x;
+            dst[(4 * q + 1) * QB] = cv[u].y;
+            dst[(4 * q + 2) * QB] = cv[u].z;
+            dst[(4 * q + 3) * QB] = cv[u].w;
+          }
+        }
       }
       __syncthreads();
-      // 4 x 4 tiles, 64 per block (a warp covers half a block: uniform branches)
-      for (int e = tid; e < S * S * 64; e += QBT) {
-        const int sl = e >> 6, t = e & 63, ia = sl / S, ib = sl % S;
-        const int i = 4 * ia + pr, j = 4 * ib + pc;
-        if (j <= k || j > i || i >= nb) continue;
-        const int r0 = (t >> 3) << 2, c0 = (t & 7) << 2;
-        const float* li = LiT + (size_t)ia * 1024 + r0;
-        const float* lj = LjT + (size_t)ib * 1024 + c0;
-        float acc[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-#pragma unroll 8
-        for (int m = 0; m < QB; ++m) {
-          const float4 x = *(const float4*)(li + m * QB);
-          const float4 y = *(const float4*)(lj + m * QB);
-          const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xs[u], ys[v], acc[u][v]);
-        }
-        float* T = slots + (size_t)sl * 1024;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int row = r0 + u;
-          float4* pp = (float4*)(T + row * QB + ((((c0 >> 2) ^ row) & 7) << 2));
-          float4 o = *pp;
-          o.x -= acc[u][0];
-          o.y -= acc[u][1];
-          o.z -= acc[u][2];
-          o.w -= acc[u][3];
-          *pp = o;
+      // lookahead: the owner of diagonal block k + 1 updates it first with warp 0 and
+      // factors it there, while its other warps and the other CTAs update the rest
+      const int kn = k + 1;
+      const bool la = kn < nb && pr == (kn & 3) && pc == (kn & 3);
+      const int sl_la = la ? (kn >> 2) * S + (kn >> 2) : -1;
+      if (la && wid == 0) {
+        float* T = slots + (size_t)sl_la * 1024;
+        const float* li = LiT + (size_t)(kn >> 2) * 1024;
+        const float* lj = LjT + (size_t)(kn >> 2) * 1024;
+        trail_tile(li, lj, T, lane);
+        trail_tile(li, lj, T, lane + 32);
+        __syncwarp();
+        factor_diag_block(T, inv, s_l, thr_of(kn), lane);
+      } else {
+        // 4 x 4 tiles, 64 per block; a warp's 32 consecutive tiles lie in one block
+        // (uniform branches), also with warp 0 left out
+        const int t0 = la ? tid - 32 : tid, nt = la ? QBT - 32 : QBT;
+        for (int e = t0; e < S * S * 64; e += nt) {
+          const int sl = e >> 6, t = e & 63, ia = sl / S, ib = sl % S;
+          const int i = 4 * ia + pr, j = 4 * ib + pc;
+          if (sl == sl_la || j <= k || j > i || i >= nb) continue;
+          trail_tile(LiT + (size_t)ia * 1024, LjT + (size_t)ib * 1024, slots + (size_t)sl * 1024, t);
         }
       }
       __syncthreads();
