@@ -404,9 +404,15 @@ __global__ void __launch_bounds__(CBT) chol_block_kernel(const double* __restric
 // is at most max(thr_rel * K_jj, thr_abs * scale): thr_rel * K_jj is the rounding
 // noise of the FP32 elimination relative to the column's own diagonal, thr_abs
 // * scale the caller's absolute threshold; (B) the owners of the panel blocks
-// (i, k), i > k, solve L_ik L_kk^T = A_ik, a thread per row; (C) every CTA
-// applies the rank-32 update to its trailing blocks from transposed copies of
-// the panel blocks.  Two cluster barriers per step.
+// (i, k), i > k, solve L_ik L_kk^T = A_ik, a thread per row, and also write
+// them transposed to a global (L2) panel buffer; (C) every CTA applies the
+// rank-32 update to its trailing blocks from transposed copies of the panel
+// blocks, and the owner of block (k + 1, k + 1) updates that block first with
+// one warp and factors it (step A of k + 1) while its other warps and the other
+// CTAs finish the update (lookahead).  Two cluster barriers per step.  The
+// panel buffer is the output buffer (written only after the last step); when
+// it is too small for nb blocks the panel is read from the owners' shared
+// memory instead.
 constexpr int QB = 32;           // block size
 constexpr int QBT = 512;         // threads per CTA
 constexpr int kCoreMaxN = 768;   // 6 x 6 blocks per CTA: the most that fit in shared memory
