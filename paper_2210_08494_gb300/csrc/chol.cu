@@ -410,9 +410,10 @@ __global__ void __launch_bounds__(CBT) chol_block_kernel(const double* __restric
 // blocks, and the owner of block (k + 1, k + 1) updates that block first with
 // one warp and factors it (step A of k + 1) while its other warps and the other
 // CTAs finish the update (lookahead).  Two cluster barriers per step.  The
-// panel buffer is the output buffer (written only after the last step); when
-// it is too small for nb blocks the panel is read from the owners' shared
-// memory instead.
+// panel buffer is the output buffer (written only after the last step); the
+// path that reads the panel from the owners' shared memory instead is kept for
+// an output too small for nb blocks (with the sizes the launchers accept this
+// happens only when nb = 1, where no panel is read).
 constexpr int QB = 32;           // block size
 constexpr int QBT = 512;         // threads per CTA
 constexpr int kCoreMaxN = 768;   // 6 x 6 blocks per CTA: the most that fit in shared memory
