@@ -2,7 +2,7 @@
 investigation of Sec. 5): how far each low-rank inverse representation is from
 the exact damped inverse of the EA K-factors, step by step.
 
-    python -m paper_2210_08494_gb300.error_study --steps 60 --out gpurun_out/error_study.json
+    python -m paper_2210_08494_gb300.error_study --steps 60 --out error_study.json
 
 One FC layer (A: d_in + 1 = 513, Gamma: 256), n = 32 new columns per step,
 rho = 0.95, rank r = 64, damping relative to the largest eigenvalue
