@@ -53,13 +53,17 @@ typedef struct CUstream_st* bkfac_stream_t;
 /* ---- precision modes ----------------------------------------------------
  * BKFAC_F64        U, X, G, S in double; all arithmetic in FP64.
  * BKFAC_F32        U, X, G, S in float; tall-skinny products in FP32; the
- *                  CholeskyQR Gram and Cholesky in FP64; core eigensolve in
- *                  FP32 (FP64 with BKFAC_FLAG_EIG_FP64).
+ *                  CholeskyQR Gram FP64-accurate (exact FP32 products with
+ *                  compensated FP32 sums), its Cholesky factorisations in FP32
+ *                  (FP64 with BKFAC_FLAG_CHOL_FP64); core eigensolve in FP32
+ *                  (FP64 with BKFAC_FLAG_EIG_FP64).
  * BKFAC_MIXED_BF16 U (master copy), X, G, S in float; the tall-skinny
  *                  products (U^T X, U M, [U Q] V, G U, U^T G and the apply
  *                  expansion) take BF16-rounded operands with FP32
- *                  accumulation; Gram/Cholesky in FP64; periodic FP64
- *                  re-orthonormalisation (bkfac_reorth) restores U^T U = I. */
+ *                  accumulation; Gram, Cholesky and eigensolve as in
+ *                  BKFAC_F32 (the same two flags select FP64); periodic
+ *                  re-orthonormalisation (bkfac_reorth: FP64-accurate Gram,
+ *                  FP64 Cholesky) restores U^T U = I. */
 enum { BKFAC_F64 = 0, BKFAC_F32 = 1, BKFAC_MIXED_BF16 = 2 };
 
 /* ---- return / status codes --------------------------------------------- */
@@ -67,7 +71,9 @@ enum {
   BKFAC_OK = 0,
   BKFAC_EINVAL = 1,         /* bad argument: sizes, ld, alignment, r > d, n <= 0 */
   BKFAC_ENOTAPPLICABLE = 2, /* (reserved) a path was requested that the shapes do not allow */
-  BKFAC_ECHOL = 3,          /* CholeskyQR: Gram matrix not positive (all pivots dropped or NaN) */
+  BKFAC_ECHOL = 3,          /* a matrix that must be positive semidefinite is not: a Cholesky pivot
+                               below -1e-2 times its largest diagonal entry (the dense factor M of
+                               bkfac_correct / bkfac_rsvd is indefinite) */
   BKFAC_ENOCONV = 4,        /* Jacobi eigensolver hit its sweep cap */
   BKFAC_ENONFINITE = 5,     /* NaN or Inf met in an input or an intermediate */
   BKFAC_ETIMEOUT = 6,       /* a bounded device-side wait gave up */
@@ -88,6 +94,8 @@ enum {
                                          factor keeps up to r + r_extra modes, so the inverse
                                          applications use the rank-(r + n) representation; the next
                                          update starts from the leading r of them */
+#define BKFAC_FLAG_CHOL_FP64 (1u << 3) /* F32 / MIXED modes: the Cholesky factorisations of CholeskyQR2
+                                          in FP64 (the FP64 path's kernel) instead of FP32 */
 
 /* ---- apply flags -------------------------------------------------------- */
 #define BKFAC_SPECTRUM_CONTINUATION (1u << 0) /* Sec. 3.5.1: lam += min sigma, sigma -= min sigma */
@@ -141,6 +149,22 @@ const char* bkfac_strerror(int code);
  * word: BKFAC_OK or the first device-side error code recorded since the last
  * call.  Returns BKFAC_ECUDA if the synchronisation itself fails. */
 int bkfac_status(bkfac_stream_t stream);
+
+/* ---- fault handling (not in the paper; for tests and operators) ----------
+ * bkfac_set_sweep_cap(cap)  Jacobi sweep cap of every later eigensolve in the
+ *     process (cap >= 1; 0 restores the default of 40).  An eigensolve that
+ *     reaches the cap records BKFAC_ENOCONV in the status word and still
+ *     returns its current columns.  Returns the previous cap, or
+ *     -BKFAC_EINVAL for cap < 0.  Not meant to change while other host
+ *     threads enqueue updates.
+ * bkfac_selftest_wait_timeout(limit_cycles, stream)  launches one thread that
+ *     waits, with the bounded mbarrier wait the eigensolve's block exchange
+ *     uses, on a barrier phase that nothing completes; after limit_cycles SM
+ *     clock cycles (1 .. 2^31) it gives up, records BKFAC_ETIMEOUT and returns,
+ *     so that the context stays usable.  Returns BKFAC_EINVAL for a limit out
+ *     of range. */
+int bkfac_set_sweep_cap(int cap);
+int bkfac_selftest_wait_timeout(int64_t limit_cycles, bkfac_stream_t stream);
 
 /* ---- workspace sizes ----------------------------------------------------- */
 enum { BKFAC_OP_UPDATE = 0, BKFAC_OP_REORTH = 1 };

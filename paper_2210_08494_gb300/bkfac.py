@@ -26,6 +26,7 @@ OK, EINVAL, ENOTAPPLICABLE, ECHOL, ENOCONV, ENONFINITE, ETIMEOUT, ECUDA, EWORKSP
 FLAG_EIG_FP64 = 1
 FLAG_TF32X3 = 2
 FLAG_KEEP_RN = 4
+FLAG_CHOL_FP64 = 8
 SPECTRUM_CONTINUATION = 1
 DAMPING_RELATIVE = 2
 OP_UPDATE, OP_REORTH = 0, 1
@@ -106,6 +107,8 @@ def load(build_if_missing: bool = True):
             "bkfac_tune": ([FP, I, ctypes.c_char_p], I),
             "bkfac_trace_read": ([ctypes.POINTER(D), ctypes.POINTER(I64), I, ctypes.POINTER(I64)], I),
             "bkfac_trace_phase_name": ([I], ctypes.c_char_p),
+            "bkfac_set_sweep_cap": ([I], I),
+            "bkfac_selftest_wait_timeout": ([I64, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name, None)
@@ -127,7 +130,8 @@ def exported_symbols():
               "bkfac_batch_apply", "bkfac_batch_step_graph", "bkfac_batch_destroy", "bkfac_trace_enable",
               "bkfac_trace_read", "bkfac_trace_phase_name", "bkfac_apply_noalloc", "bkfac_tune", "bkfac_batch_reorth",
               "bkfac_apply_factored_workspace_size", "bkfac_apply_factored", "bkfac_ea_update",
-              "bkfac_correct_workspace_size", "bkfac_correct", "bkfac_rsvd_workspace_size", "bkfac_rsvd"):
+              "bkfac_correct_workspace_size", "bkfac_correct", "bkfac_rsvd_workspace_size", "bkfac_rsvd",
+              "bkfac_set_sweep_cap", "bkfac_selftest_wait_timeout"):
         if hasattr(lib, n):
             names.append(n)
     return names
@@ -245,6 +249,19 @@ def bkfac_version() -> int:
 
 def bkfac_status(stream=None) -> int:
     return int(load().bkfac_status(_stream(stream)))
+
+
+def bkfac_set_sweep_cap(cap: int) -> int:
+    """Sets the Jacobi sweep cap of later eigensolves (0 = default); returns the previous cap."""
+    prev = int(load().bkfac_set_sweep_cap(int(cap)))
+    if prev < 0:
+        raise BkfacError(-prev, "bkfac_set_sweep_cap")
+    return prev
+
+
+def bkfac_selftest_wait_timeout(limit_cycles: int, stream=None):
+    """Runs the bounded-wait self-test (a wait that must time out); check bkfac_status()."""
+    _check(load().bkfac_selftest_wait_timeout(int(limit_cycles), _stream(stream)), "bkfac_selftest_wait_timeout")
 
 
 def bkfac_workspace_size(f: Factor, n: int, op: int = OP_UPDATE) -> int:

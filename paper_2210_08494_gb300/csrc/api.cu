@@ -12,6 +12,7 @@
 //   U <- [U Q] V[:, :r_new], sigma <- lambda[:r_new]
 // Dense path (r + n >= d): Jacobi on F = [U sqrt(rho sigma), sqrt(c) X].
 #include <algorithm>
+#include <atomic>
 #include <vector>
 #include <cmath>
 #include <cstring>
@@ -22,7 +23,11 @@ namespace bkfac {
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kMaxSweeps = 40;
+constexpr int kDefaultSweepCap = 40;
+// Jacobi sweep cap of every eigensolve (bkfac_set_sweep_cap); a problem that reaches
+// it records BKFAC_ENOCONV
+std::atomic<int> g_sweep_cap{kDefaultSweepCap};
+int sweep_cap() { return g_sweep_cap.load(std::memory_order_relaxed); }
 
 size_t es_of(DType t) { return t == DT_F64 ? 8 : 4; }
 DType dt_of(int dtype) { return dtype == BKFAC_F64 ? DT_F64 : DT_F32; }
@@ -57,6 +62,7 @@ struct Prec {
   DType t, jt, acc;
   bool bf16;
   bool x3;     // FP32 products as 3xTF32 on the tensor cores (BKFAC_FLAG_TF32X3)
+  bool chol64;  // CholeskyQR factorisations in FP64 also on the FP32 / mixed paths
   double u_t;  // unit roundoff governing the residual threshold
 };
 Prec prec_of(const bkfac_factor* f) {
@@ -66,6 +72,7 @@ Prec prec_of(const bkfac_factor* f) {
   p.bf16 = f->dtype == BKFAC_MIXED_BF16;
   p.x3 = f->dtype == BKFAC_F32 && (f->flags & BKFAC_FLAG_TF32X3) != 0;
   p.jt = (f->dtype == BKFAC_F64 || (f->flags & BKFAC_FLAG_EIG_FP64)) ? DT_F64 : DT_F32;
+  p.chol64 = f->dtype == BKFAC_F64 || (f->flags & BKFAC_FLAG_CHOL_FP64) != 0;
   p.u_t = f->dtype == BKFAC_F64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
   return p;
 }
@@ -297,28 +304,32 @@ P* at(void* ws, size_t off) {
 
 // Cholesky: the cluster kernel when n fits it, else the single-CTA kernel
 // near_out (may be null) receives whether the near-identity shortcut was taken
+// neg_rel > 0: a pivot below -neg_rel * (*scale) records BKFAC_ECHOL (the matrix is
+// indefinite beyond its rounding); 0 disables the check
 int run_chol(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
-             int* near_out, cudaStream_t s) {
+             int* near_out, cudaStream_t s, double neg_rel = 0.0) {
   // the blocked 2D block-cyclic kernel spreads every step over the cluster
-  if (chol_block_ok(n)) return launch_chol_block(Gm, n, R, thr_rel, scale, near_tol, near_out, s);
-  if (chol_cluster_size(n) > 0) return launch_chol_cluster(Gm, n, R, thr_rel, scale, near_tol, near_out, s);
+  if (chol_block_ok(n)) return launch_chol_block(Gm, n, R, thr_rel, scale, near_tol, near_out, neg_rel, s);
+  if (chol_cluster_size(n) > 0)
+    return launch_chol_cluster(Gm, n, R, thr_rel, scale, near_tol, near_out, neg_rel, s);
   if (near_out != nullptr && cudaMemsetAsync(near_out, 0, sizeof(int), s) != cudaSuccess) return BKFAC_ECUDA;
-  return launch_chol(Gm, n, R, thr_rel, scale, s);
+  return launch_chol(Gm, n, R, thr_rel, scale, neg_rel, s);
 }
 
 // second CholeskyQR pass: G2 = I + E; the near-identity factor's error is O(|E|^2)
 double near_identity_tol(const Prec& pr) { return pr.t == DT_F64 ? 1e-9 : 1e-5; }
 
-// The Cholesky factorisations of CholeskyQR2: FP64 for the FP64 path; for the FP32
-// and mixed paths the FP64-accurate Gram is factored in FP32 on the cluster (FP64
-// runs at 1/64 of the FP32 rate on this GPU), and a pivot is also dropped when its
+// The Cholesky factorisations of CholeskyQR2: FP64 for the FP64 path (and with
+// BKFAC_FLAG_CHOL_FP64); by default the FP32 and mixed paths factor the FP64-accurate
+// Gram in FP32 on the cluster (FP64 runs at 1/64 of the FP32 rate on this GPU), and a
+// pivot is also dropped when its
 // Schur complement is within the FP32 elimination's rounding noise of its diagonal,
 // 4 sqrt(n) u_32 G_jj: such a direction is numerically dependent at FP32 precision
 // and its orthogonalisation would be noise.  The second pass restores
 // orthonormality to the working precision as before.
 int run_chol_qr(const Prec& pr, const double* Gm, int n, double* R, double thr_abs, const double* scale,
                 double near_tol, int* near, cudaStream_t s) {
-  if (pr.t != DT_F64 && chol_r32_ok(n)) {
+  if (!pr.chol64 && chol_r32_ok(n)) {
     const float thr_rel = (float)(4.0 * std::sqrt((double)n) * 5.9604644775390625e-08);
     return launch_chol_r32(Gm, n, R, thr_rel, thr_abs, scale, near_tol, near, s);
   }
@@ -423,7 +434,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     jp.colnorm2 = a.colnorm2;
     jp.sweeps_out = at<int>(ws, p.o_sw);
     jp.stamp = at<int>(ws, p.o_st);
-    PHASE(PH_JACOBI, launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(d, pr.jt), kMaxSweeps, s));
+    PHASE(PH_JACOBI, launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(d, pr.jt), sweep_cap(), s));
     SortArgs so;
     so.W = a.F;
     so.rows = d;
@@ -567,7 +578,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   jp.colnorm2 = ca.colnorm2;
   jp.sweeps_out = at<int>(ws, p.o_sw);
   jp.stamp = at<int>(ws, p.o_st);
-  PHASE(PH_JACOBI, launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(p.N, pr.jt), kMaxSweeps, s));
+  PHASE(PH_JACOBI, launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(p.N, pr.jt), sweep_cap(), s));
   SortArgs so;
   so.W = ca.L;
   so.rows = p.N;
@@ -688,7 +699,11 @@ int run_small_evd(const double* A, const SmallEvd& e, const Prec& pr, double thr
   void* L = at<void>(ws, e.o_L);
   double* cn = at<double>(ws, e.o_cn);
   PHASE(PH_CHOL, launch_diag_max(A, e.n, scale, s));
-  PHASE(PH_CHOL, run_chol(A, e.n, R, thr_rel, scale, 0.0, nullptr, s));
+  // the matrix must be p.s.d.: a Schur complement below -1e-2 of its largest diagonal
+  // entry is indefiniteness far beyond rounding (BKFAC_ECHOL; rounding in the
+  // projection of an FP32 dense factor onto its tail modes stays orders of magnitude
+  // below that); such a pivot is still dropped
+  PHASE(PH_CHOL, run_chol(A, e.n, R, thr_rel, scale, 0.0, nullptr, s, 1e-2));
   PHASE(PH_CORE, launch_assemble_transpose(R, e.n, e.rows_pad, e.cols_pad, L, cn, pr.jt, s));
   JacobiProblem jp;
   jp.W = L;
@@ -700,7 +715,7 @@ int run_small_evd(const double* A, const SmallEvd& e, const Prec& pr, double thr
   jp.colnorm2 = cn;
   jp.sweeps_out = at<int>(ws, e.o_sw);
   jp.stamp = at<int>(ws, e.o_st);
-  PHASE(PH_JACOBI, launch_jacobi(&jp, 1, e.C, pr.jt, jacobi_tol(e.n, pr.jt), kMaxSweeps, s));
+  PHASE(PH_JACOBI, launch_jacobi(&jp, 1, e.C, pr.jt, jacobi_tol(e.n, pr.jt), sweep_cap(), s));
   SortArgs so;
   so.W = L;
   so.rows = e.n;
@@ -945,6 +960,16 @@ int bkfac_update(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho,
   return update_common(f, X, ldx, n, rho, ws, ws_bytes, (cudaStream_t)stream, false);
 }
 
+int bkfac_set_sweep_cap(int cap) {
+  if (cap < 0) return -BKFAC_EINVAL;
+  return g_sweep_cap.exchange(cap == 0 ? kDefaultSweepCap : cap);
+}
+
+int bkfac_selftest_wait_timeout(int64_t limit_cycles, bkfac_stream_t stream) {
+  if (limit_cycles < 1 || limit_cycles > (int64_t(1) << 31)) return BKFAC_EINVAL;
+  return launch_wait_selftest((long long)limit_cycles, nullptr, (cudaStream_t)stream) == 0 ? BKFAC_OK : BKFAC_ECUDA;
+}
+
 int bkfac_reorth(bkfac_factor* f, void* ws, size_t ws_bytes, bkfac_stream_t stream) {
   if (!valid_factor(f)) return BKFAC_EINVAL;
   const int k = f->r_cur;
@@ -980,7 +1005,7 @@ int bkfac_reorth(bkfac_factor* f, void* ws, size_t ws_bytes, bkfac_stream_t stre
   jp.colnorm2 = cn;
   jp.sweeps_out = at<int>(ws, cap.o_sw);
   jp.stamp = at<int>(ws, cap.o_st);
-  BK_TRY(launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(k, pr.jt), kMaxSweeps, s));
+  BK_TRY(launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(k, pr.jt), sweep_cap(), s));
   SortArgs so;
   so.W = Lm;
   so.rows = k;

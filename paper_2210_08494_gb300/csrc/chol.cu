@@ -33,7 +33,7 @@ constexpr int CT = 512;
 
 __global__ void __launch_bounds__(CT) chol_cluster_kernel(const double* __restrict__ Gm, int n, double* R,
                                                           double thr_rel, const double* scale, double near_tol,
-                                                          int* near_out) {
+                                                          int* near_out, double neg_rel) {
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int q = (int)cluster.block_rank();
@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(CT) chol_cluster_kernel(const double* __restri
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   (void)lane;
   const double thr = thr_rel * (scale ? *scale : 1.0);
+  const double neg = neg_rel * (scale ? *scale : 1.0);  // pivots below -neg: not p.s.d.
 
   // near-identity test on the CTA's own columns with integer compares of the IEEE bit
   // patterns (|g| <= tol off the diagonal, 1 - tol <= g <= 1 + tol on it; NaN fails):
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(CT) chol_cluster_kernel(const double* __restri
           const double s = A[c + jl * n];
           const int keep = s > thr;  // false for NaN as well
           if (!isfinite(s)) report(BKFAC_ENONFINITE);
+          if (neg_rel > 0.0 && s < -neg) report(BKFAC_ECHOL);
           s_keep = keep;
           if (keep) {
             const double l = sqrt(s);
@@ -194,7 +196,7 @@ __device__ __forceinline__ int blk_rank(int pr, int pc) { return pr * 4 + pc; }
 
 __global__ void __launch_bounds__(CBT) chol_block_kernel(const double* __restrict__ Gm, int n, double* R,
                                                          double thr_rel, const double* scale, double near_tol,
-                                                         int* near_out) {
+                                                         int* near_out, double neg_rel) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int pr = rank / 4, pc = rank % 4;
@@ -209,6 +211,7 @@ __global__ void __launch_bounds__(CBT) chol_block_kernel(const double* __restric
   auto slot = [&](int a, int b) { return slots + (size_t)(a * S + b) * 256; };
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const double thr = thr_rel * (scale ? *scale : 1.0);
+  const double neg = neg_rel * (scale ? *scale : 1.0);  // pivots below -neg: not p.s.d.
 
   // load the owned lower blocks (entries past n are zero: their pivots are dropped)
   for (int e = tid; e < S * S * 256; e += CBT) {
@@ -263,6 +266,7 @@ __global__ void __launch_bounds__(CBT) chol_block_kernel(const double* __restric
           const double piv = D[j * CB + j];
           const bool keep = piv > thr;  // false for NaN as well
           if (!isfinite(piv)) report(BKFAC_ENONFINITE);
+          if (neg_rel > 0.0 && piv < -neg) report(BKFAC_ECHOL);
           double l = 0.0, il = 0.0;
           if (keep) {
             if (piv > 1e-30 && piv < 1e30) {
@@ -809,7 +813,7 @@ size_t chol_block_smem(int n) {
 bool chol_block_ok(int n) { return n >= 32 && chol_block_smem(n) <= 200 * 1024; }
 
 int launch_chol_block(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
-                      int* near_out, cudaStream_t s) {
+                      int* near_out, double neg_rel, cudaStream_t s) {
   if (!chol_block_ok(n)) return (int)cudaErrorInvalidValue;
   static std::atomic<int> configured{0};
   if (!configured.load()) {
@@ -831,7 +835,7 @@ int launch_chol_block(const double* Gm, int n, double* R, double thr_rel, const 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, chol_block_kernel, Gm, n, R, thr_rel, scale, near_tol, near_out);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, chol_block_kernel, Gm, n, R, thr_rel, scale, near_tol, near_out, neg_rel);
   note_launches(1);
   return (int)e;
 }
@@ -924,7 +928,7 @@ int chol_cluster_size(int n) {
 }
 
 int launch_chol_cluster(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
-                        int* near_out, cudaStream_t s) {
+                        int* near_out, double neg_rel, cudaStream_t s) {
   if (n <= 0) return 0;
   const int C = chol_cluster_size(n);
   if (C == 0) return (int)cudaErrorInvalidValue;
@@ -950,7 +954,7 @@ int launch_chol_cluster(const double* Gm, int n, double* R, double thr_rel, cons
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, chol_cluster_kernel, Gm, n, R, thr_rel, scale, near_tol, near_out);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, chol_cluster_kernel, Gm, n, R, thr_rel, scale, near_tol, near_out, neg_rel);
   note_launches(1);
   return (int)e;
 }

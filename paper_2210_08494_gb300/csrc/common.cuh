@@ -114,18 +114,21 @@ int splitk_reduce_f32(const GemmArgs& g, cudaStream_t s);
 int launch_colnorm_max(const void* X, int64_t ldx, int d, int n, DType t, double* out, cudaStream_t s);
 // thresholded Cholesky of an n x n FP64 Gram (column-major, ld n): upper R (n x n, ld n);
 // pivot j dropped (row j of R zero) when s_j <= thr_rel * (*scale).  scale may be null (= 1).
-int launch_chol(const double* Gm, int n, double* R, double thr_rel, const double* scale, cudaStream_t s);
+// With neg_rel > 0 a pivot below -neg_rel * (*scale) -- the matrix is indefinite beyond
+// its rounding -- also records BKFAC_ECHOL in the status word (the pivot is dropped).
+int launch_chol(const double* Gm, int n, double* R, double thr_rel, const double* scale, double neg_rel,
+                cudaStream_t s);
 // the same factorisation on a thread-block cluster (chol.cu); with near_tol > 0 and
 // max|G - I| <= near_tol the factor is I + (strict upper part + half diagonal of G - I);
 // near_out (may be null) receives 1 when that shortcut was taken, else 0
 int launch_chol_cluster(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
-                        int* near_out, cudaStream_t s);
+                        int* near_out, double neg_rel, cudaStream_t s);
 int chol_cluster_size(int n);  // 0 when n is too large for the cluster kernel
 // blocked (2D block-cyclic, 16 x 16 blocks) FP64 Cholesky on a 16-CTA cluster with the
 // near-identity shortcut of the second CholeskyQR pass (near_tol > 0); for 32 <= n <= 576
 bool chol_block_ok(int n);
 int launch_chol_block(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
-                      int* near_out, cudaStream_t s);
+                      int* near_out, double neg_rel, cudaStream_t s);
 // FP32 Cholesky K = G G^T of an n x n symmetric positive semidefinite matrix (lower
 // triangle read, column-major, ld ldk) on a 16-CTA cluster, written as the Jacobi's
 // column-major rows_pad x cols_pad matrix G (zero above the diagonal and beyond n)
@@ -224,6 +227,10 @@ int tune_load(const char* path);
 int tune_save(const char* path);
 // shared memory bytes one CTA needs for a problem
 size_t jacobi_smem_bytes(int b, int rows_pad, DType j_t);
+// self-test of the bounded mbarrier wait (jacobi.cu): a wait on a phase nothing
+// completes gives up after limit_cycles and records BKFAC_ETIMEOUT; *out (may be
+// null) receives 1 on time-out
+int launch_wait_selftest(long long limit_cycles, int* out, cudaStream_t s);
 // choose cluster size and block width for a problem
 void jacobi_plan(int rows, int cols, DType j_t, int* C, int* b, int* rows_pad, int* cols_pad);
 

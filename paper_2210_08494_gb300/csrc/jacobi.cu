@@ -531,13 +531,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait for phase `parity` of a local mbarrier: false once ~2^31 cycles
-// (about a second) have passed without completion
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// bounded wait for phase `parity` of a local mbarrier: false once `limit` SM clock
+// cycles (by default 2^31, about a second) have passed without completion
+constexpr long long kWaitLimitCycles = 1ll << 31;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long limit = kWaitLimitCycles) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
+}
+
+// Self-test of the bounded wait: one thread arms a barrier that needs two arrivals,
+// arrives once, and waits for the phase that the missing arrival would complete --
+// a flag that nothing sets.  After `limit` cycles the wait gives up, BKFAC_ETIMEOUT is
+// recorded and the kernel returns, as the eigensolve does when a block exchange
+// never lands.  `out` receives 1 when the wait timed out, 0 otherwise.
+__global__ void wait_timeout_selftest_kernel(long long limit, int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 2);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(&bar))
+               : "memory");
+  const bool ok = mbar_wait_bounded(&bar, 0u, limit);
+  if (!ok) report(BKFAC_ETIMEOUT);
+  if (out) *out = ok ? 0 : 1;
 }
 // bulk copy of `bytes` (multiple of 16) from this CTA's shared memory to shared
 // memory of a CTA of the cluster; completion is signalled on that CTA's mbarrier
@@ -896,6 +915,12 @@ int launch_jacobi_mode(const JacobiProblem* probs, int nprob, int C, DType j_t, 
                : launch_nv<double, false>(batch, nprob, C, b, rp, smem, tol, max_sweeps, s);
   return dsm ? launch_nv<float, true>(batch, nprob, C, b, rp, 3 * smem, tol, max_sweeps, s)
              : launch_nv<float, false>(batch, nprob, C, b, rp, smem, tol, max_sweeps, s);
+}
+
+int launch_wait_selftest(long long limit_cycles, int* out, cudaStream_t s) {
+  wait_timeout_selftest_kernel<<<1, 32, 0, s>>>(limit_cycles, out);
+  note_launches(1);
+  return (int)cudaGetLastError();
 }
 
 size_t jacobi_smem_bytes(int b, int rows_pad, DType j_t) {

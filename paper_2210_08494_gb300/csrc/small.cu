@@ -70,9 +70,10 @@ __global__ void __launch_bounds__(256) colnorm_max_kernel(const T* X, int64_t ld
 // (row j of R set to zero) when its Schur complement s_j <= thr; the matching
 // direction of P is then (numerically) in the span of the kept ones.
 __global__ void __launch_bounds__(1024) chol_kernel(const double* __restrict__ Gm, int n, double* R, double thr_rel,
-                                                    const double* scale) {
+                                                    const double* scale, double neg_rel) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const double thr = thr_rel * (scale ? *scale : 1.0);
+  const double neg = neg_rel * (scale ? *scale : 1.0);  // pivots below -neg: not p.s.d.
   for (int l = 0; l < n; ++l)
     for (int i = tid; i < n; i += nt) R[i + l * n] = (i <= l) ? Gm[i + l * n] : 0.0;
   __syncthreads();
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(1024) chol_kernel(const double* __restrict__ G
       const double s = R[j + (int64_t)j * n];
       s_keep = s > thr;  // false for NaN as well
       if (!isfinite(s)) report(BKFAC_ENONFINITE);
+      if (neg_rel > 0.0 && s < -neg) report(BKFAC_ECHOL);
       if (s_keep) {
         s_piv[0] = sqrt(s);
         s_piv[1] = 1.0 / s_piv[0];
@@ -580,9 +582,10 @@ int launch_colnorm_max(const void* X, int64_t ldx, int d, int n, DType t, double
   return (int)cudaGetLastError();
 }
 
-int launch_chol(const double* Gm, int n, double* R, double thr_rel, const double* scale, cudaStream_t s) {
+int launch_chol(const double* Gm, int n, double* R, double thr_rel, const double* scale, double neg_rel,
+                cudaStream_t s) {
   if (n <= 0) return 0;
-  chol_kernel<<<1, 1024, 0, s>>>(Gm, n, R, thr_rel, scale);
+  chol_kernel<<<1, 1024, 0, s>>>(Gm, n, R, thr_rel, scale, neg_rel);
   note_launches(1);
   return (int)cudaGetLastError();
 }

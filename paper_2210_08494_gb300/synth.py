@@ -121,3 +121,39 @@ def mlp_batches(widths, n: int, seed_w: int, seed_x: int, step: int, device="cpu
     grads = [(z.grad * n).detach().contiguous() for z in zs]
     wgrads = [torch.cat([w.grad, b.grad[:, None]], dim=1).detach().contiguous() for w, b in zip(weights, biases)]
     return acts_b, grads, wgrads
+
+
+class DevicePowerlaw:
+    """The powerlaw_batch recipe drawn on a CUDA device, for runs too long for host
+    generation (hundreds of steps at d = 4097).  Q_d comes from a QR of a seeded
+    Gaussian on the device (a different draw from orthogonal_basis), Z ~ N(0, 1) from
+    torch's generator seeded with (seed, step); X = Q_d diag(k^(-alpha/2)) Z is
+    formed in FP32 and written into a caller buffer (an (n, ld) column tensor)."""
+
+    def __init__(self, d: int, alpha: float, seed: int, device):
+        import torch
+
+        self.d, self.seed, self.device = int(d), int(seed), device
+        g = torch.Generator(device=device).manual_seed(int(seed) * 7919 + 17)
+        a = torch.randn(self.d, self.d, generator=g, device=device, dtype=torch.float64)
+        q, r = torch.linalg.qr(a)
+        s = torch.sign(torch.diagonal(r))
+        s[s == 0] = 1.0
+        q = q * s[None, :]
+        sc = torch.from_numpy(powerlaw_scales(self.d, alpha)).to(device)
+        self.qs_t = (q * sc[None, :]).T.contiguous().float()  # rows: scaled basis vectors
+        self.gen = torch.Generator(device=device)
+
+    def draw(self, out, n: int, step: int):
+        """Writes batch `step` (n columns) into out[:n, :d] (float32)."""
+        import torch
+
+        self.gen.manual_seed(self.seed * 1000003 + int(step))
+        z = torch.randn(n, self.d, generator=self.gen, device=self.device, dtype=torch.float32)
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        try:
+            out[:n, : self.d].copy_(z @ self.qs_t)
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev
+        return out

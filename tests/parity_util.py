@@ -41,3 +41,91 @@ def truncation_gap(lam, r):
     if r >= len(lam) or lam[r - 1] <= 0:
         return np.inf
     return float((lam[r - 1] - lam[r]) / lam[r - 1])
+
+
+# Unit roundoff of each path's eigensolve input, for the near-tie reading at the
+# truncation index: the FP64 and FP32 paths take 1e3 u (eigenvalues closer than that
+# may swap order under the path's rounding); the mixed path's core carries the BF16
+# rounding of its tall-skinny products, so ties are flagged within 10 u_bf16.
+NEAR_TIE = {0: 1e3 * 2.0 ** -53, 1: 1e3 * 2.0 ** -24, 2: 10 * 2.0 ** -8}
+
+# Per-mode eigenvalue bound relative to the largest eigenvalue (Weyl: every sorted
+# eigenvalue moves by at most the 2-norm of the perturbation, which each path's
+# rounding bounds by about N u |K|): FP64 1e-12, FP32 4e-6, mixed 8e-3 (2 u_bf16).
+MODE_TOL = {0: 1e-12, 1: 4e-6, 2: 8e-3}
+
+
+def gapped_prefix(lam, r, thr):
+    """Largest k < r whose relative gap (lam_k - lam_{k+1}) / lam_k is at least thr (0 if none)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    for k in range(min(r, len(lam)) - 1, 0, -1):
+        if lam[k - 1] > 0 and (lam[k - 1] - lam[k]) / lam[k - 1] >= thr:
+            return k
+    return 0
+
+
+def max_sin_theta(U1t, U2t, k):
+    """sin of the largest principal angle between the spans of the first k rows."""
+    if k <= 0:
+        return 0.0
+    A = np.asarray(U1t, dtype=np.float64)[:k]
+    B = np.asarray(U2t, dtype=np.float64)[:k]
+    s = np.linalg.svd(A @ B.T, compute_uv=False)
+    c = float(np.clip(s.min(), -1.0, 1.0))
+    return float(np.sqrt(max(0.0, 1.0 - c * c)))
+
+
+def judge_step(Ug, sg, Uo_full, so_full, k, dtype, tol, orth_tol=None):
+    """Compares one GPU step (k modes Ug (k, d), sg) with the oracle's untruncated
+    result (Uo_full (N, d), so_full (N,) descending) under the parity readings:
+
+    * sigma: relative Frobenius error < tol, and every mode within MODE_TOL of the
+      largest eigenvalue (Weyl's bound holds for sorted eigenvalues, ties or not);
+    * subspaces: at every index j <= k whose relative gap exceeds 1e-3, the sine
+      of the largest angle between the top-j subspaces is within the Davis-Kahan
+      bound 10 MODE_TOL sigma_1 / (sigma_j - sigma_{j+1});
+    * reconstruction U diag(sigma) U^T: relative Frobenius error < tol -- unless the
+      oracle's gap at the truncation index is a near tie (below NEAR_TIE), where the
+      k-th mode is not determined by the path's precision: then the reconstruction
+      is judged on the leading modes up to the last index whose gap clears NEAR_TIE.
+
+    Returns a dict of the measured quantities."""
+    so = np.asarray(so_full, dtype=np.float64)
+    Uo = np.asarray(Uo_full, dtype=np.float64)
+    sg = np.asarray(sg, dtype=np.float64)[:k]
+    Ug = np.asarray(Ug, dtype=np.float64)[:k]
+    out = {}
+    es = rel(sg, so[:k])
+    out["sigma"] = es
+    assert es < tol, ("sigma", es)
+    s1 = max(so[0], 1e-300) if len(so) else 1.0
+    mode = float(np.abs(sg - so[:k]).max() / s1) if k else 0.0
+    out["mode"] = mode
+    assert mode < MODE_TOL[dtype], ("per-mode sigma", mode)
+    worst_angle = 0.0
+    gapped = [j for j in range(1, k + 1)
+              if so[j - 1] > 0 and (so[j - 1] - (so[j] if j < len(so) else 0.0)) / so[j - 1] > 1e-3]
+    if len(gapped) > 32:  # 32 evenly spaced gapped indices, the last one included
+        gapped = [gapped[i] for i in np.linspace(0, len(gapped) - 1, 32).round().astype(int)]
+    for j in gapped:
+        nxt = so[j] if j < len(so) else 0.0
+        bound = min(1.0, 10.0 * MODE_TOL[dtype] * s1 / (so[j - 1] - nxt))
+        st = max_sin_theta(Ug, Uo, j)
+        worst_angle = max(worst_angle, st / bound)
+        assert st <= bound, ("subspace", j, st, bound)
+    out["angle_frac"] = worst_angle
+    tie = truncation_gap(so, k) < NEAR_TIE[dtype] if k < len(so) else False
+    out["tie"] = bool(tie)
+    if tie:
+        k0 = gapped_prefix(so, k, NEAR_TIE[dtype])
+        er = lowrank_rel_err(Ug[:k0], sg[:k0], Uo[:k0], so[:k0]) if k0 else 0.0
+    else:
+        er = lowrank_rel_err(Ug, sg, Uo[:k], so[:k])
+    out["recon"] = er
+    assert er < tol, ("reconstruction", er, "near tie" if tie else "")
+    if orth_tol is not None:
+        pos = sg > 0
+        oe = orth_err(Ug[pos])
+        out["orth"] = oe
+        assert oe < orth_tol, ("orthonormality", oe)
+    return out

@@ -15,7 +15,7 @@ import pytest
 import torch
 
 from paper_2210_08494_gb300 import bkfac, synth
-from tests.parity_util import lowrank_rel_err, orth_err, rel
+from tests.parity_util import NEAR_TIE, lowrank_rel_err, orth_err, rel, truncation_gap
 from tests.test_gpu_update import check_status, gpu_state, one_step_parity, rounded, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -107,33 +107,44 @@ def test_preconditioned_batch_in_span(oracle):
 
 
 def test_preconditioned_trajectory_stays_close(oracle):
-    """Free-running trajectory (both sides from the same first batch) over 6 steps."""
+    """Free-running trajectory (both sides from the same first batch) over 6 steps.
+    Trajectory parity: the FP32 path's 1e-4 applies to the final state when no step
+    met a near tie at the truncation index (relative gap below 1e3 u_32), where the
+    r-th mode is not determined by FP32 rounding and the trajectories may keep
+    different r-th modes; the oracle keeps every mode of each step to see the gap."""
     d, r, n = 1024, 128, 64
     f = bkfac.Factor(d, r, bkfac.F32)
     X0 = synth.powerlaw_batch(d, 2 * r, 1.2, 12, 0)
     bkfac.bkfac_init(f, to_dev(X0, f))
     check_status()
-    Uo, so, info = oracle.init(rounded(X0, f), r)
-    Uo, so = Uo[: info["r_new"]], so[: info["r_new"]]
+    Uo, so, info = oracle.init(rounded(X0, f), 2 * r)
+    min_gap = truncation_gap(so[: info["r_new"]], r)
+    Uo, so = Uo[:r], so[:r]
     for t in range(1, 7):
         X = synth.powerlaw_batch(d, n, 1.2, 12, t)
         bkfac.bkfac_update(f, to_dev(X, f), 0.95)
         check_status()
-        Uo, so, info = oracle.update(Uo, so, Uo.shape[0], rounded(X, f), 0.95, r)
-        Uo, so = Uo[: info["r_new"]], so[: info["r_new"]]
+        Uo, so, info = oracle.update(Uo, so, Uo.shape[0], rounded(X, f), 0.95, r + n)
+        min_gap = min(min_gap, truncation_gap(so[: info["r_new"]], r))
+        Uo, so = Uo[:r], so[:r]
     U2, s2 = gpu_state(f)
-    assert rel(s2, so) < 1e-3
-    assert lowrank_rel_err(U2, s2, Uo, so) < 1e-3
+    es, er = rel(s2, so), lowrank_rel_err(U2, s2, Uo, so)
+    print(f"FP32 trajectory after 6 steps: sigma {es:.2e} reconstruction {er:.2e} (min truncation gap {min_gap:.2e})")
+    assert min_gap > NEAR_TIE[bkfac.F32]
+    assert es < 1e-4 and er < 1e-4
 
 
-@pytest.mark.parametrize("eps", [1e-5, 3e-3])
+@pytest.mark.parametrize("eps", [1e-5, 5e-4, 8e-4, 1.1e-3, 1.4e-3, 1.8e-3, 2.5e-3, 3e-3])
 def test_fp32_choleskyqr_nearly_dependent_columns(oracle, eps):
     """Batch columns that repeat others up to a relative perturbation eps: the residual
     is ill-conditioned (kappa ~ 1/eps).  The FP32 and mixed paths factor its FP64 Gram
-    in FP32: at eps = 1e-5 the repeated directions fall below the FP32 elimination's
-    noise and are dropped (their energy, ~eps^2 of a column's, is far below the
+    in FP32 and drop pivot j when its Schur complement is within 4 sqrt(n) u_32 of its
+    diagonal, i.e. for a direction independent of the others by less than
+    sqrt(4 sqrt(64) u_32) ~ 1.4e-3 of its residual norm here: at eps = 1e-5 the repeated
+    directions are dropped (their energy, ~eps^2 of a column's, is far below the
     tolerance); at eps = 3e-3 they are kept and the second CholeskyQR pass restores
-    orthonormality."""
+    orthonormality; the values in between straddle the point where the kept-or-dropped
+    decision flips, where parity must hold either way."""
     d, r, n = 900, 96, 64
     f = bkfac.Factor(d, r, bkfac.F32)
     X0 = synth.powerlaw_batch(d, 2 * r, 1.2, 21, 0)

@@ -7,26 +7,30 @@ rho = 0.95; every A and Gamma factor updated and every layer preconditioned by
 one captured CUDA graph (the launch configuration the benchmark times for the
 batch API).  The output layer's Gamma (d = 10) takes the dense path.
 
-Sampled parity: before the compared replay the state of a few factors is read
-back; the oracle repeats that step from the same state on the same batch, and
-the preconditioned gradient of the sampled layers is compared with the
-oracle's inverse application on the updated state.  Both are relative
-Frobenius errors: 1e-4 for FP32, 2e-2 for the mixed BF16 path.
+Parity on every layer: before the compared replay the state of all 32 factors
+is read back; the oracle repeats that step from the same state on the same
+batch (tests.parity_util.judge_step: sigma, per-mode and subspace bounds,
+reconstruction with the near-tie reading), and every layer's preconditioned
+gradient is compared with the oracle's inverse application on the updated
+state, in relative Frobenius norm and element by element (the largest
+|S - S_o| over the largest |S_o|, which a localised error in one output tile of
+the tensor-core or SIMT GEMMs would fail).  Tolerances: 1e-4 for FP32, 1e-2 for
+one step of the mixed BF16 path.
 """
 import numpy as np
 import pytest
 import torch
 
 from paper_2210_08494_gb300 import bkfac, synth
-from tests.parity_util import lowrank_rel_err, orth_err, rel
+from tests.parity_util import judge_step, orth_err, rel
 
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(513, 1024), (1025, 2048), (2049, 4096), (4097, 4096), (4097, 10)]
 RANKS = [64, 128, 256]
 NL, N, RHO, ALPHA, LAM = 16, 128, 0.95, 1.2, 1e-2
-SAMPLED = [2, 4, 8]  # (2049, 4096, r 256), (4097, 10, r 128 -> dense Gamma), (4097, 4096, r 256)
-TOL = {bkfac.F32: 1e-4, bkfac.MIXED_BF16: 2e-2}
+SAMPLED = list(range(NL))
+TOL = {bkfac.F32: 1e-4, bkfac.MIXED_BF16: 1e-2}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -115,23 +119,27 @@ def test_uneven_batch_graph_step_matches_oracle(oracle, inputs, dtype):
             U0, s0 = before[(l, w)]
             X = torch.from_numpy(steps[3][l][w]).float().double().numpy()  # the values the GPU received
             upd = oracle.update_dense if f.r + N >= d else oracle.update
-            Uo, so, info = upd(U0, s0, U0.shape[0], X, RHO, f.r)
-            k = info["r_new"]
+            kin = U0.shape[0]
+            Uo, so, info = upd(U0, s0, kin, X, RHO, min(kin + N, d))
+            k = min(f.r, info["r_new"])
             assert f.r_cur == k
             U, s = f.state()
             Ug, sg = U.double().cpu().numpy(), s.cpu().numpy()
-            es, er = rel(sg, so[:k]), lowrank_rel_err(Ug, sg, Uo[:k], so[:k])
-            report.append("layer %d %s d=%d r=%d: sigma %.2e reconstruction %.2e" % (l, "AG"[w], d, f.r, es, er))
-            assert es < tol and er < tol, (l, w, es, er)
             # U' = [U Q] V is an FP32 product over K = r + n <= 384 terms: its departure
             # from orthonormality is O(K u_f32) = 2.3e-5 per step on top of the
             # Jacobi tolerance; 1e-4 is the FP32 path's tolerance
-            assert orth_err(Ug) < (1e-4 if dtype == bkfac.F32 else 2e-2), (l, w)
-            post.append((Ug, sg))
+            m = judge_step(Ug, sg, Uo[: info["r_new"]], so[: info["r_new"]], k, dtype, tol,
+                           orth_tol=1e-4 if dtype == bkfac.F32 else 2e-2)
+            report.append("layer %d %s d=%d r=%d: sigma %.2e per-mode %.2e reconstruction %.2e%s"
+                          % (l, "AG"[w], d, f.r, m["sigma"], m["mode"], m["recon"], " (near tie)" if m["tie"] else ""))
+            post.append((Ug[:k], sg[:k]))
         (UA, sA), (UG, sG) = post
         So = oracle.apply(UA, sA, LAM, UG, sG, LAM, grads[l])
-        ea = rel(S[l].double().cpu().numpy(), So)
-        report.append("layer %d apply %d x %d gradient: %.2e" % (l, dG, dA, ea))
+        Sg = S[l].double().cpu().numpy()
+        ea = rel(Sg, So)
+        em = float(np.abs(Sg - So).max() / np.abs(So).max())
+        report.append("layer %d apply %d x %d gradient: %.2e (elementwise %.2e)" % (l, dG, dA, ea, em))
         assert ea < tol, (l, ea)
+        assert em < tol, (l, em)
     print("\n".join(report))
     batch.close()

@@ -7,19 +7,24 @@ batch (rounded to the path's dtype), so each step's tolerance applies to that
 step alone.  Trajectory parity: both run free from the same first batch.
 
 Tolerances (relative Frobenius): 1e-10 for the FP64 path, 1e-4 for the FP32
-path, 2e-2 for the mixed BF16 path (operand rounding u_bf16 = 2^-8 in each
-tall-skinny product, FP32 accumulation).
+path, 1e-2 for one step of the mixed BF16 path (operand rounding u_bf16 = 2^-8
+in each tall-skinny product, FP32 accumulation: a one-step result moves by a
+few tenths of u_bf16 to about u_bf16; 1e-2 is 2.5 u_bf16).  Each step is
+judged by tests.parity_util.judge_step: relative sigma and reconstruction
+errors, every eigenvalue within the path's Weyl bound, the top-j subspaces at
+gapped indices within their Davis-Kahan bound, and the near-tie reading at the
+truncation index.
 """
 import numpy as np
 import pytest
 import torch
 
 from paper_2210_08494_gb300 import bkfac, synth
-from tests.parity_util import lowrank_rel_err, orth_err, rel, truncation_gap
+from tests.parity_util import judge_step, lowrank_rel_err, orth_err, rel, truncation_gap
 
 pytestmark = pytest.mark.gpu
 
-TOL = {bkfac.F64: 1e-10, bkfac.F32: 1e-4, bkfac.MIXED_BF16: 2e-2}
+TOL = {bkfac.F64: 1e-10, bkfac.F32: 1e-4, bkfac.MIXED_BF16: 1e-2}
 ORTH = {bkfac.F64: 1e-12, bkfac.F32: 2e-5, bkfac.MIXED_BF16: 2e-2}
 
 
@@ -54,36 +59,40 @@ def check_status():
     assert st == bkfac.OK, bkfac.strerror(st)
 
 
-def one_step_parity(oracle, d, r, n, dtype, rho=0.95, steps=4, alpha=1.5, seed=1, flags=0, orth=None):
+def one_step_parity(oracle, d, r, n, dtype, rho=0.95, steps=4, alpha=1.5, seed=1, flags=0, orth=None, tol=None):
+    """Init, then `steps` updates; before each update the oracle starts from the GPU's
+    state.  The oracle keeps every mode (no truncation) so that the truncation gap and
+    the per-mode bounds can be judged; returns (factor, worst relative error)."""
     f = bkfac.Factor(d, r, dtype, flags=flags)
     dense = r + n >= d
-    tol = TOL[dtype]
+    tol = TOL[dtype] if tol is None else tol
+    orth_tol = ORTH[dtype] if orth is None else orth
     X0 = synth.powerlaw_batch(d, n, alpha, seed, 0)
     bkfac.bkfac_init(f, to_dev(X0, f))
     check_status()
-    Uo, so, info = oracle.init(rounded(X0, f), r, dense=dense)
+    Uo, so, info = oracle.init(rounded(X0, f), min(n, d), dense=dense)
     Ug, sg = gpu_state(f)
-    k = info["r_new"]
+    k = min(r, info["r_new"])
     assert f.r_cur == k
-    assert rel(sg, so[:k]) < tol
-    assert lowrank_rel_err(Ug, sg, Uo[:k], so[:k]) < tol
-    worst = 0.0
+    m = judge_step(Ug, sg, Uo[:info["r_new"]], so[:info["r_new"]], k, dtype, tol)
+    worst, ties, mode = max(m["sigma"], m["recon"]), int(m["tie"]), m["mode"]
     for t in range(1, steps + 1):
         Ug, sg = gpu_state(f)
         X = synth.powerlaw_batch(d, n, alpha, seed, t)
         bkfac.bkfac_update(f, to_dev(X, f), rho)
         check_status()
         upd = oracle.update_dense if dense else oracle.update
-        Uo, so, info = upd(Ug, sg, Ug.shape[0], rounded(X, f), rho, r)
-        k = info["r_new"]
+        kin = Ug.shape[0]
+        full = min(kin + n, d)
+        Uo, so, info = upd(Ug, sg, kin, rounded(X, f), rho, full)
+        k = min(r, info["r_new"])
         assert f.r_cur == k
         U2, s2 = gpu_state(f)
-        es = rel(s2, so[:k])
-        er = lowrank_rel_err(U2, s2, Uo[:k], so[:k])
-        worst = max(worst, es, er)
-        assert es < tol, (t, es)
-        assert er < tol, (t, er)
-        assert orth_err(U2[s2 > 0]) < (ORTH[dtype] if orth is None else orth)
+        m = judge_step(U2, s2, Uo[:info["r_new"]], so[:info["r_new"]], k, dtype, tol, orth_tol=orth_tol)
+        worst = max(worst, m["sigma"], m["recon"])
+        ties += int(m["tie"])
+        mode = max(mode, m["mode"])
+    print(f"d={d} r={r} n={n} dtype={dtype}: worst {worst:.2e}, per-mode {mode:.2e}, near ties {ties}")
     return f, worst
 
 
@@ -194,7 +203,9 @@ def test_trajectory_f64_small_factor(oracle):
         Ug, sg = gpu_state(f)
         err = lowrank_rel_err(Ug, sg, Uo[:k], so[:k])
         print(f"d={d}: trajectory error after {steps} steps {err:.3e} (min truncation gap {min_gap:.2e})")
-        assert err < 1e-9
+        # no step came within the FP64 near-tie threshold (1e3 u) of swapping the r-th mode
+        assert min_gap > 1e3 * 2.0 ** -53
+        assert err < 1e-10
         sides.append((f, Uo[:k], so[:k]))
     (fA, UA, sA), (fG, UG, sG) = sides
     Gn = synth.gradient(256, 512, 1002, 0)
@@ -206,7 +217,7 @@ def test_trajectory_f64_small_factor(oracle):
     So = oracle.apply(UA, sA, 0.1, UG, sG, 0.1, Gn)
     ea = rel(S.cpu().numpy(), So)
     print(f"apply after {steps} steps: relative error {ea:.3e}")
-    assert ea < 1e-9
+    assert ea < 1e-10
 
 
 def test_update_in_span_drops_residual(oracle):
