@@ -219,6 +219,32 @@ def update(Ut, sigma, k: int, Xt, rho: float, r: int):
     return _update(_load().bko_update, Ut, sigma, k, Xt, rho, r)
 
 
+def update_eigh(Ut, sigma, k: int, Xt, rho: float, r: int):
+    """The update of ``update`` with LAPACK's symmetric eigensolver (numpy ``eigh``) in
+    place of the two-sided Jacobi for the core's eigendecomposition (step 4 of the
+    Brand update); projection, pivoted Householder QR, the core of Eq. (7) and the
+    rotation are the oracle's own steps.  For long trajectories, where the Jacobi's
+    cost dominates; pinned to ``update`` in tests/test_oracle_pins.py."""
+    Xt = _f64(Xt)
+    n, d = Xt.shape
+    Uk = _f64(Ut)[:k] if k else np.zeros((0, d))
+    sk = _f64(sigma)[:k]
+    M, Pt = project(Uk, Xt)
+    tol = 1e-12 * float(np.sqrt(np.max(np.sum(Xt * Xt, axis=1))))
+    Qt, R, m = qrcp(Pt, tol)
+    MS = core(sk, rho, (1.0 - rho) / n, M, R)
+    w, V = np.linalg.eigh(MS)
+    order = np.argsort(-w, kind="stable")  # descending, ties: lower index first
+    w, V = w[order], V[:, order]
+    N = k + n
+    r_new = min(r, N)
+    Uo = np.zeros((r, d))
+    so = np.zeros(r)
+    Uo[:r_new] = V[:, :r_new].T @ np.concatenate([Uk, Qt], axis=0)
+    so[:r_new] = w[:r_new]
+    return Uo, so, {"r_new": r_new, "rank_p": m, "sweeps": 0, "N": N}
+
+
 def update_dense(Ut, sigma, k: int, Xt, rho: float, r: int):
     """Dense update (r + n >= d): explicit K and its top-r eigenpairs."""
     return _update(_load().bko_update_dense, Ut, sigma, k, Xt, rho, r)

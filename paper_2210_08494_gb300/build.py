@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbkfac.so")
-SOURCES = ["api.cu", "gemm.cu", "tc_gemm.cu", "small.cu", "jacobi.cu", "chol.cu", "trace.cu", "batch.cu", "tune.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "gemm.cu", "tc_gemm.cu", "small.cu", "jacobi.cu", "chol.cu", "trace.cu", "batch.cu", "tune.cu", "noalloc.cu", "tma_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

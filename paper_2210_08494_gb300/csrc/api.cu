@@ -105,7 +105,16 @@ size_t partial_bytes(int M, int N, int K, size_t acc_es) {
   return (size_t)32 * std::max(M, 1) * std::max(N, 1) * acc_es;
 }
 
-UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
+// the eigensolve's launch shape: the tuned one for the shape (jacobi_plan), or the
+// block-width cap of a caller's choice (a batch's grouped eigensolves)
+void plan_jacobi(int rows, int cols, DType jt, const JacobiChoice* jc, int* C, int* b, int* rp, int* cp) {
+  if (jc && jc->b_max > 0)
+    jacobi_plan_with(rows, cols, jt, jc->b_max, C, b, rp, cp);
+  else
+    jacobi_plan(rows, cols, jt, C, b, rp, cp);
+}
+
+UpdatePlan plan_update(const bkfac_factor* f, int n, int k, const JacobiChoice* jc = nullptr) {
   UpdatePlan p{};
   p.pr = prec_of(f);
   p.d = f->d;
@@ -120,7 +129,7 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
   if (p.dense) {
     p.N = k + n;
     p.r_new = std::min(std::min(r_total(f), k + n), f->d);
-    jacobi_plan(f->d, k + n, p.pr.jt, &p.C, &p.b, &p.rows_pad, &p.cols_pad);
+    plan_jacobi(f->d, k + n, p.pr.jt, jc, &p.C, &p.b, &p.rows_pad, &p.cols_pad);
     int C2, b2, rp2, cp2;
     jacobi_plan(f->d, f->r + n, p.pr.jt, &C2, &b2, &rp2, &cp2);
     rows_cap = rp2;
@@ -136,7 +145,7 @@ UpdatePlan plan_update(const bkfac_factor* f, int n, int k) {
     p.r_new = std::min(r_total(f), k + n);
     p.ldm = std::max(kmax, 1);
     p.ldv = round_up(Nmax, 4);
-    jacobi_plan(p.N, p.N, p.pr.jt, &p.C, &p.b, &p.rows_pad, &p.cols_pad);
+    plan_jacobi(p.N, p.N, p.pr.jt, jc, &p.C, &p.b, &p.rows_pad, &p.cols_pad);
     int C2, b2, rp2, cp2;
     jacobi_plan(Nmax, Nmax, p.pr.jt, &C2, &b2, &rp2, &cp2);
     rows_cap = rp2;
@@ -219,7 +228,15 @@ struct ApplyPlan {
   int64_t ld1, ld2, ldw;
   size_t o_T1, o_T2, o_T3, o_W1, o_part, o_part1, o_cA, o_cG, o_cAo, o_cGo, o_alpha, total;
   size_t part1_bytes;
+  // mixed path on the TMA-fed tensor cores: BF16 K-major copies of the operands
+  bool tma;
+  int64_t ldgb, ldgt, ldua, ldug, ld2k;  // row pitches (elements) of Gb, Gt, UAb, UGb, A2 / B2
+  size_t o_Gb, o_Gt, o_UAb, o_UGb, o_A2, o_B2;
 };
+
+// the mixed path's apply runs on the TMA-fed tensor-core kernel (BF16 operands
+// rounded once into K-major copies) when the driver provides tensor maps
+bool apply_on_tma(const Prec& pr) { return pr.bf16 && !pr.x3 && tma_gemm_available(); }
 
 ApplyPlan plan_apply(const bkfac_factor* fA, const bkfac_factor* fG, int kA, int kG) {
   ApplyPlan p{};
@@ -248,6 +265,23 @@ ApplyPlan plan_apply(const bkfac_factor* fA, const bkfac_factor* fG, int kA, int
   p.o_cAo = L.add((size_t)rA * 8);
   p.o_cGo = L.add((size_t)rG * 8);
   p.o_alpha = L.add(8);
+  p.tma = apply_on_tma(p.pr);
+  if (p.tma) {
+    // split K of pass 1 into up to 8 pieces (T1: d_out x r_A and T2: d_in x r_G outputs)
+    p.part1_bytes = (size_t)8 * std::max((size_t)p.dG * rA, (size_t)p.dA * rG) * aes;
+    p.o_part1 = L.add(p.part1_bytes);
+    p.ldgb = bf16_ld(p.dA);
+    p.ldgt = bf16_ld(p.dG);
+    p.ldua = bf16_ld(p.dA);
+    p.ldug = bf16_ld(p.dG);
+    p.ld2k = bf16_ld(rA + rG);
+    p.o_Gb = L.add((size_t)p.dG * p.ldgb * 2);
+    p.o_Gt = L.add((size_t)p.dA * p.ldgt * 2);
+    p.o_UAb = L.add((size_t)std::max(rA, 1) * p.ldua * 2);
+    p.o_UGb = L.add((size_t)std::max(rG, 1) * p.ldug * 2);
+    p.o_A2 = L.add((size_t)p.dG * p.ld2k * 2);
+    p.o_B2 = L.add((size_t)p.dA * p.ld2k * 2);
+  }
   p.total = L.total;
   return p;
 }
@@ -372,7 +406,7 @@ int run_gram(const void* A, int64_t lda, int d, int n, Prec pr, double* G, void*
   // only the upper tiles of the symmetric output are computed: split K until about
   // two CTAs per SM are busy (at most 32 partials, at least 128 rows of K each)
   const int64_t tiles = ceil_div(n, 64), active = tiles * (tiles + 1) / 2;
-  int64_t splits = ceil_div(2 * 152, active);
+  int64_t splits = ceil_div(2 * sm_count(), active);
   splits = std::min<int64_t>(std::min<int64_t>(splits, 32), std::max<int64_t>(1, d / 128));
   g.splits = (int)std::max<int64_t>(2, splits);
   g.partial = part;
@@ -401,9 +435,12 @@ int run_trmm(const void* P, int64_t ldp, int d, int n, const void* Rinv, Prec pr
   return gemm_run(g, pr.t, pr.acc, pr.t, s);
 }
 
-// the full update sequence for one factor (k = current rank, rho, c already set)
-int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, void* ws,
-                   const UpdatePlan& p, cudaStream_t s) {
+// The update of one factor up to its eigensolve (k = current rank): the Brand path's
+// projection, residual, CholeskyQR2, core factor L (and on FP32 eigensolves the
+// Cholesky factor of the core matrix), or the dense path's factor F; *jp_out
+// receives the eigensolve's problem.
+int enqueue_update_pre(const bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, void* ws,
+                       const UpdatePlan& p, cudaStream_t s, JacobiProblem* jp_out) {
   const Prec& pr = p.pr;
   const int d = f->d, k = p.k;
   const double c = (1.0 - rho) / (double)n;
@@ -434,25 +471,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     jp.colnorm2 = a.colnorm2;
     jp.sweeps_out = at<int>(ws, p.o_sw);
     jp.stamp = at<int>(ws, p.o_st);
-    PHASE(PH_JACOBI, launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(d, pr.jt), sweep_cap(), s));
-    SortArgs so;
-    so.W = a.F;
-    so.rows = d;
-    so.rows_pad = p.rows_pad;
-    so.cols = k + n;
-    so.r_out = p.r_new;
-    so.V = f->U;
-    so.ldv = f->ldu;
-    so.sig = f->sigma;
-    so.r_sig = r_total(f);
-    so.lam_sorted = at<double>(ws, p.o_lam);
-    so.colnorm2 = a.colnorm2;
-    so.cols_pad = p.cols_pad;
-    PHASE(PH_SORT, launch_sort_output(so, pr.jt, pr.t, s));
-    // columns past r_new are cleared so U holds no stale modes
-    if (p.r_new < r_total(f)) {
-      PHASE(PH_FINALIZE, launch_finalize(f->U, f->ldu, f->U, f->ldu, d, p.r_new, r_total(f), pr.t, s));
-    }
+    *jp_out = jp;
     return BKFAC_OK;
   }
 
@@ -486,7 +505,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
     g.tf32x3 = pr.x3;
     g.C = M;
     g.ldc = p.ldm;
-    g.splits = gemm_pick_splits(k, n, d, 152);
+    g.splits = gemm_pick_splits(k, n, d, sm_count());
     g.partial = part;
     g.partial_bytes = p.part_bytes;
     PHASE(PH_PROJ, gemm_run(g, pr.t, pr.acc, pr.t, s));
@@ -578,9 +597,42 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   jp.colnorm2 = ca.colnorm2;
   jp.sweeps_out = at<int>(ws, p.o_sw);
   jp.stamp = at<int>(ws, p.o_st);
-  PHASE(PH_JACOBI, launch_jacobi(&jp, 1, p.C, pr.jt, jacobi_tol(p.N, pr.jt), sweep_cap(), s));
+  *jp_out = jp;
+  return BKFAC_OK;
+}
+
+// The rest of the update after its eigensolve: eigenvalues in decreasing order and
+// the eigenvector matrix V (Brand path) or the new U (dense path), U' = [U Q] V[:, :r_new]
+// and its write-back.  Reads the workspace the pre-eigensolve stage filled.
+int enqueue_update_post(const bkfac_factor* f, int n, void* ws, const UpdatePlan& p, cudaStream_t s) {
+  const Prec& pr = p.pr;
+  const int d = f->d, k = p.k;
+  if (p.dense) {
+    SortArgs so;
+    so.W = at<void>(ws, p.o_L);
+    so.rows = d;
+    so.rows_pad = p.rows_pad;
+    so.cols = k + n;
+    so.r_out = p.r_new;
+    so.V = f->U;
+    so.ldv = f->ldu;
+    so.sig = f->sigma;
+    so.r_sig = r_total(f);
+    so.lam_sorted = at<double>(ws, p.o_lam);
+    so.colnorm2 = at<double>(ws, p.o_cn);
+    so.cols_pad = p.cols_pad;
+    PHASE(PH_SORT, launch_sort_output(so, pr.jt, pr.t, s));
+    // columns past r_new are cleared so U holds no stale modes
+    if (p.r_new < r_total(f)) {
+      PHASE(PH_FINALIZE, launch_finalize(f->U, f->ldu, f->U, f->ldu, d, p.r_new, r_total(f), pr.t, s));
+    }
+    return BKFAC_OK;
+  }
+
+  void* Q = at<void>(ws, p.o_Q);
+  void* part = at<void>(ws, p.o_part);
   SortArgs so;
-  so.W = ca.L;
+  so.W = at<void>(ws, p.o_L);
   so.rows = p.N;
   so.rows_pad = p.rows_pad;
   so.cols = p.N;
@@ -590,7 +642,7 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   so.sig = f->sigma;
   so.r_sig = r_total(f);
   so.lam_sorted = at<double>(ws, p.o_lam);
-  so.colnorm2 = ca.colnorm2;
+  so.colnorm2 = at<double>(ws, p.o_cn);
   so.cols_pad = p.cols_pad;
   // sigma is only read by the core assembly above, so it can be overwritten here
   PHASE(PH_SORT, launch_sort_output(so, pr.jt, pr.t, s));
@@ -621,6 +673,16 @@ int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, dou
   return BKFAC_OK;
 }
 
+// The whole update of one factor: pre-eigensolve stage, the eigensolve, the rest.
+int enqueue_update(const bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, void* ws,
+                   const UpdatePlan& p, cudaStream_t s) {
+  JacobiProblem jp;
+  int rc = enqueue_update_pre(f, X, ldx, n, rho, ws, p, s, &jp);
+  if (rc) return rc;
+  PHASE(PH_JACOBI, launch_jacobi(&jp, 1, p.C, p.pr.jt, jacobi_tol(jp.rows, p.pr.jt), sweep_cap(), s));
+  return enqueue_update_post(f, n, ws, p, s);
+}
+
 int check_ws(void* ws, size_t ws_bytes, size_t need) {
   if (need == 0) return BKFAC_OK;
   if (!ws || ((uintptr_t)ws) % kAlign != 0 || ws_bytes < need) return BKFAC_EWORKSPACE;
@@ -634,8 +696,10 @@ bool jacobi_fits(int rows, int C, int b, int rows_pad, DType jt) {
   return rows <= rows_pad && b <= 32 && jacobi_smem_bytes(b, rows_pad, jt) <= 200 * 1024;
 }
 
-int update_common(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, void* ws, size_t ws_bytes,
-                  cudaStream_t s, bool init) {
+// argument checks and the plan of one update (k = the modes it starts from); the plan
+// of the largest rank sizes the workspace
+int plan_checked(const bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, void* ws, size_t ws_bytes,
+                 bool init, const JacobiChoice* jc, UpdatePlan* out) {
   if (!valid_factor(f) || !X || n < 1 || ldx < f->d) return BKFAC_EINVAL;
   const size_t es = f->dtype == BKFAC_F64 ? 8 : 4;
   if (((uintptr_t)X) % 16 != 0 || (ldx * (int64_t)es) % 16 != 0) return BKFAC_EINVAL;
@@ -645,12 +709,21 @@ int update_common(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho
   // BKFAC_FLAG_KEEP_RN the factor may hold more after the previous one)
   const int k = init ? 0 : std::min(f->r_cur, f->r);
   const UpdatePlan cap = plan_update(f, n, f->r);
-  UpdatePlan p = plan_update(f, n, k);
+  UpdatePlan p = plan_update(f, n, k, jc);
   p.total = cap.total;
   if (p.rows_pad > p.rows_cap || p.cols_pad > p.cols_cap) return BKFAC_EINVAL;
   if (!jacobi_fits(p.dense ? f->d : p.N, p.C, p.b, p.rows_pad, p.pr.jt)) return BKFAC_EINVAL;
   if (p.N > 8192 || (!p.dense && n > 1024)) return BKFAC_EINVAL;
-  int rc = check_ws(ws, ws_bytes, cap.total);
+  const int rc = check_ws(ws, ws_bytes, cap.total);
+  if (rc) return rc;
+  *out = p;
+  return BKFAC_OK;
+}
+
+int update_common(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, void* ws, size_t ws_bytes,
+                  cudaStream_t s, bool init) {
+  UpdatePlan p;
+  int rc = plan_checked(f, X, ldx, n, rho, ws, ws_bytes, init, nullptr, &p);
   if (rc) return rc;
   rc = enqueue_update(f, X, ldx, n, init ? 0.0 : rho, ws, p, s);
   if (rc) return rc;
@@ -799,7 +872,7 @@ int run_cross_f64(const void* A, int64_t lda, const void* B, int64_t ldb, int d,
   g.b_kmaj = true;
   g.C = C;
   g.ldc = m;
-  g.splits = gemm_pick_splits(m, m, d, 152);
+  g.splits = gemm_pick_splits(m, m, d, sm_count());
   g.partial = part;
   return gemm_run(g, pr.t, DT_F64, DT_F64, s);
 }
@@ -895,6 +968,35 @@ int run_orth(const void* Y, int d, int l, const RsvdPlan& p, void* ws, void* Q, 
 }
 
 }  // namespace
+
+// ---- staged updates for the batch: pre-eigensolve stage, grouped eigensolves, rest
+int update_stage_pre(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, bool init, void* ws,
+                     size_t ws_bytes, const JacobiChoice* jc, cudaStream_t s, StagedEig* out) {
+  UpdatePlan p;
+  int rc = plan_checked(f, X, ldx, n, rho, ws, ws_bytes, init, jc, &p);
+  if (rc) return rc;
+  rc = enqueue_update_pre(f, X, ldx, n, init ? 0.0 : rho, ws, p, s, &out->jp);
+  if (rc) return rc;
+  out->C = p.C;
+  out->jt = p.pr.jt;
+  out->tol = jacobi_tol(out->jp.rows, p.pr.jt);
+  return BKFAC_OK;
+}
+
+int update_stage_post(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, bool init, void* ws,
+                      size_t ws_bytes, const JacobiChoice* jc, cudaStream_t s) {
+  UpdatePlan p;
+  int rc = plan_checked(f, X, ldx, n, rho, ws, ws_bytes, init, jc, &p);
+  if (rc) return rc;
+  rc = enqueue_update_post(f, n, ws, p, s);
+  if (rc) return rc;
+  f->r_cur = p.r_new;
+  f->step = init ? 1 : f->step + 1;
+  return BKFAC_OK;
+}
+
+int eig_sweep_cap() { return sweep_cap(); }
+
 }  // namespace bkfac
 
 using namespace bkfac;
@@ -1082,8 +1184,39 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
   ca.betaA = nullptr;
   ca.betaG = nullptr;
   PHASE(PH_COEFS, launch_apply_coefs(ca, s));
+  if (cap.tma) {
+    // BF16 K-major copies: G and G^T from one read of G, the bases U_A and U_G
+    void* Gb = at<void>(ws, cap.o_Gb);
+    void* Gt = at<void>(ws, cap.o_Gt);
+    void* UAb = at<void>(ws, cap.o_UAb);
+    void* UGb = at<void>(ws, cap.o_UGb);
+    PHASE(PH_APPLY1, launch_cvt_both((const float*)G, ldg, dG, dA, Gb, cap.ldgb, Gt, cap.ldgt, s));
+    PHASE(PH_APPLY1, launch_cvt_cols((const float*)fA->U, fA->ldu, dA, kA, UAb, cap.ldua, s));
+    PHASE(PH_APPLY1, launch_cvt_cols((const float*)fG->U, fG->ldu, dG, kG, UGb, cap.ldug, s));
+    if (kA > 0) {  // T1 = G U_A: A = G (rows i, K = j), B = U_A (rows = modes, K = j)
+      GemmArgs g = gemm_base();
+      g.M = dG;
+      g.N = kA;
+      g.C = T1;
+      g.ldc = cap.ld1;
+      g.partial = at<void>(ws, cap.o_part1);
+      g.partial_bytes = cap.part1_bytes;
+      PHASE(PH_APPLY1, tma_gemm_run(Gb, cap.ldgb, UAb, cap.ldua, dA, g, s));
+    }
+    if (kG > 0) {  // T2 (d_in x kG column-major) = G^T U_G scaled by C_G / lamA': A = G^T, B = U_G
+      GemmArgs g = gemm_base();
+      g.M = dA;
+      g.N = kG;
+      g.C = T2;
+      g.ldc = cap.ld2;
+      g.cs = cGo;
+      g.partial = at<void>(ws, cap.o_part1);
+      g.partial_bytes = cap.part1_bytes;
+      PHASE(PH_APPLY1, tma_gemm_run(Gt, cap.ldgt, UGb, cap.ldug, dG, g, s));
+    }
+  }
   // pass 1: T1 = G U_A (d_out x kA), T2 = diag(C_G / lamA') U_G^T G (kG x d_in, row-major)
-  if (kA > 0) {
+  if (kA > 0 && !cap.tma) {
     GemmArgs g = gemm_base();
     g.M = dG;
     g.N = kA;
@@ -1102,7 +1235,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.partial_bytes = cap.part1_bytes;
     PHASE(PH_APPLY1, gemm_run(g, pr.t, pr.acc, pr.t, s));
   }
-  if (kG > 0) {
+  if (kG > 0 && !cap.tma) {
     GemmArgs g = gemm_base();
     g.M = dA;
     g.N = kG;
@@ -1139,7 +1272,7 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
       g.ldc = cap.ldw;
       g.rs = cG;
       g.cs = cA;
-      g.splits = gemm_pick_splits(kG, kA, dG, 152);
+      g.splits = gemm_pick_splits(kG, kA, dG, sm_count());
       g.partial = at<void>(ws, cap.o_part);
       g.partial_bytes = partial_bytes(r_total(fG), r_total(fA), dG, es_of(pr.acc));
       PHASE(PH_APPLY_SMALL, gemm_run(g, pr.t, pr.acc, pr.t, s));
@@ -1163,7 +1296,26 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     PHASE(PH_APPLY_SMALL, gemm_run(g, pr.t, pr.acc, pr.t, s));
   }
   // pass 2: S = alpha G + W1 U_A^T + U_G W2
-  {
+  if (cap.tma) {
+    // A2 = [W1 | U_G] (d_out x (kA + kG)) and B2 = [U_A | T2] (d_in x (kA + kG)), K-major BF16
+    void* A2 = at<void>(ws, cap.o_A2);
+    void* B2 = at<void>(ws, cap.o_B2);
+    PHASE(PH_APPLY2, launch_cvt_cat_t((const float*)W1, cap.ld1, kA, (const float*)fG->U, fG->ldu, kG, dG, A2,
+                                      cap.ld2k, s));
+    PHASE(PH_APPLY2, launch_cvt_cat_t((const float*)fA->U, fA->ldu, kA, (const float*)T2, cap.ld2, kG, dA, B2,
+                                      cap.ld2k, s));
+    GemmArgs g = gemm_base();
+    g.M = dG;
+    g.N = dA;
+    g.C = S;
+    g.ldc = lds;
+    g.c_rowmaj = true;
+    g.D = G;
+    g.ldd = ldg;
+    g.beta_dev = alpha;
+    g.beta = 1.0;
+    PHASE(PH_APPLY2, tma_gemm_run(A2, cap.ld2k, B2, cap.ld2k, kA + kG, g, s));
+  } else {
     GemmArgs g = gemm_base();
     g.M = dG;
     g.N = dA;
@@ -1278,7 +1430,7 @@ int bkfac_apply_factored(const bkfac_factor* fA, const bkfac_factor* fG, double 
       g.C = sd.T;
       g.ldc = sd.ldt;
       g.rs = sd.c;
-      g.splits = gemm_pick_splits(sd.k, n, d, 152);
+      g.splits = gemm_pick_splits(sd.k, n, d, sm_count());
       g.partial = at<void>(ws, p.o_part);
       g.partial_bytes = p.part_bytes;
       PHASE(PH_FACT_THIN, gemm_run(g, pr.t, pr.acc, pr.t, s));

@@ -2,12 +2,15 @@
 //
 // A batch owns, allocated once at creation: one device workspace carved into
 // per-factor update workspaces and per-layer apply workspaces, one worker
-// stream per factor, the fork/join events, and (after a capture) a CUDA graph
-// of one full step.  A batched update forks every factor's update onto its
-// worker stream from the caller's stream and joins them back, so the factors'
-// kernels run concurrently; the apply does the same per layer.  Captured once,
-// the whole step (every update, then every apply) replays as a single graph
-// launch.
+// stream per factor, the fork/join events, the launch choice of each group of
+// same-shape eigensolves, and (after a capture) a CUDA graph of one full step.
+// A batched update runs in three stages: every factor's update up to its
+// eigensolve, forked onto the factors' worker streams; the eigensolves, one
+// grouped launch per group of factors with the same eigensolve shape (each
+// cluster of the launch takes one factor's problem); the rest of every update
+// (ordering, rotation, write-back), forked again.  The apply forks per layer.
+// Captured once, the whole step (every update, then every apply) replays as a
+// single graph launch.
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
@@ -30,6 +33,10 @@ struct bkfac_batch {
   cudaGraphExec_t exec = nullptr;
   int64_t graph_kernels = 0;  // kernels one replay of the graph launches
   int device = -1;
+  // grouped eigensolves: factors with the same eigensolve shape at the steady rank
+  // (rows, columns, precision) share a launch choice, tuned per group size
+  std::vector<int> group;                   // per factor: its group
+  std::vector<bkfac::JacobiChoice> choice;  // per group
 };
 
 namespace {
@@ -62,28 +69,76 @@ int join_into(bkfac_batch* b, cudaStream_t s, int count) {
   return BKFAC_OK;
 }
 
-// one-CTA-per-SM clusters of 16 that fit on the GPU at once
-constexpr int kClustersAtOnce = 152 / 16;
-
+// Stage 1 forks every factor's update up to its eigensolve; stage 2 launches the
+// eigensolves grouped by launch shape (b, padded rows, cluster size, precision, rows),
+// one launch per group (up to kMaxJacobiProblems problems each), the groups forked
+// onto worker streams so they run concurrently; stage 3 forks the rest of every
+// update.  Every stage joins back into the caller's stream.
 int batch_update(bkfac_batch* b, const void* const* X_A, const int64_t* ldxA, const void* const* X_G,
                  const int64_t* ldxG, double rho, cudaStream_t s) {
   const int nf = 2 * b->nl;
-  int rc = fork_from(b, s, nf);
+  std::vector<bkfac::StagedEig> st(nf);
+  std::vector<char> init(nf), ok(nf, 0);
+  auto X_of = [&](int i) { return (i & 1) ? X_G[i / 2] : X_A[i / 2]; };
+  auto ld_of = [&](int i) { return (i & 1) ? ldxG[i / 2] : ldxA[i / 2]; };
   int first_err = BKFAC_OK;
+  int rc = fork_from(b, s, nf);
   if (rc) return rc;
-  bkfac::jacobi_set_many_concurrent(nf > kClustersAtOnce);
   for (int i = 0; i < nf; ++i) {
-    const int l = i / 2;
-    const void* X = (i & 1) ? X_G[l] : X_A[l];
-    const int64_t ld = (i & 1) ? ldxG[l] : ldxA[l];
-    void* ws = (char*)b->ws + b->ws_off[i];
-    bkfac_factor* f = &b->f[i];
-    rc = f->r_cur == 0 ? bkfac_init(f, X, ld, b->n, ws, b->ws_len[i], (bkfac_stream_t)b->streams[i])
-                       : bkfac_update(f, X, ld, b->n, rho, ws, b->ws_len[i], (bkfac_stream_t)b->streams[i]);
+    init[i] = b->f[i].r_cur == 0;
+    rc = bkfac::update_stage_pre(&b->f[i], X_of(i), ld_of(i), b->n, rho, init[i], (char*)b->ws + b->ws_off[i],
+                                 b->ws_len[i], &b->choice[b->group[i]], b->streams[i], &st[i]);
+    if (rc && !first_err) first_err = rc;
+    ok[i] = rc == BKFAC_OK;
+  }
+  rc = join_into(b, s, nf);  // always join, so the caller's stream waits for whatever was enqueued
+  if (first_err || rc) return first_err ? first_err : rc;
+  // stage 2: one launch per launch shape
+  struct Launch {
+    std::vector<bkfac::JacobiProblem> probs;
+    int C;
+    bkfac::DType jt;
+    double tol;
+    int dsm;
+  };
+  std::vector<Launch> launches;
+  for (int i = 0; i < nf; ++i) {
+    const bkfac::JacobiProblem& jp = st[i].jp;
+    Launch* hit = nullptr;
+    for (auto& L : launches) {
+      const bkfac::JacobiProblem& q = L.probs[0];
+      if (L.C == st[i].C && L.jt == st[i].jt && q.b == jp.b && q.rows_pad == jp.rows_pad && q.rows == jp.rows &&
+          (int)L.probs.size() < bkfac::kMaxJacobiProblems) {
+        hit = &L;
+        break;
+      }
+    }
+    if (!hit) {
+      launches.push_back(Launch{{}, st[i].C, st[i].jt, st[i].tol, b->choice[b->group[i]].dsm});
+      hit = &launches.back();
+    }
+    hit->probs.push_back(jp);
+  }
+  const int ng = std::min((int)launches.size(), nf);
+  rc = fork_from(b, s, ng);
+  if (rc) return rc;
+  for (int g = 0; g < (int)launches.size(); ++g) {
+    const Launch& L = launches[g];
+    rc = bkfac::launch_jacobi_mode(L.probs.data(), (int)L.probs.size(), L.C, L.jt, L.tol, bkfac::eig_sweep_cap(),
+                                   L.dsm != 0, b->streams[g % ng]);
+    if (rc && !first_err) first_err = BKFAC_ECUDA;
+  }
+  rc = join_into(b, s, ng);
+  if (first_err || rc) return first_err ? first_err : rc;
+  // stage 3: the rest of every update
+  rc = fork_from(b, s, nf);
+  if (rc) return rc;
+  for (int i = 0; i < nf; ++i) {
+    rc = bkfac::update_stage_post(&b->f[i], X_of(i), ld_of(i), b->n, rho, init[i], (char*)b->ws + b->ws_off[i],
+                                  b->ws_len[i], &b->choice[b->group[i]], b->streams[i]);
     if (rc && !first_err) first_err = rc;
   }
-  bkfac::jacobi_set_many_concurrent(false);
-  rc = join_into(b, s, nf);  // always join, so the caller's stream waits for whatever was enqueued
+  rc = join_into(b, s, nf);
   return first_err ? first_err : rc;
 }
 
@@ -182,6 +237,54 @@ bkfac_batch* bkfac_batch_create(const bkfac_layer_desc* layers, int nlayers, int
   if (tune_cache) {
     for (const auto& f : b->f) bkfac_tune(&f, n, tune_cache);
   }
+  // eigensolve groups: factors whose eigensolve has the same shape at the steady rank
+  // (rows = r + n on the Brand path, d on the dense path; columns r + n; precision)
+  struct Key {
+    int rows, cols, jt;
+  };
+  std::vector<Key> keys;
+  std::vector<int> counts;
+  for (const auto& f : b->f) {
+    const int jt = (f.dtype == BKFAC_F64 || (f.flags & BKFAC_FLAG_EIG_FP64)) ? 0 : 1;
+    const bool dense = (int64_t)f.r + n >= f.d;
+    const Key k{dense ? f.d : f.r + n, f.r + n, jt};
+    int g = 0;
+    while (g < (int)keys.size() && !(keys[g].rows == k.rows && keys[g].cols == k.cols && keys[g].jt == k.jt)) ++g;
+    if (g == (int)keys.size()) {
+      keys.push_back(k);
+      counts.push_back(0);
+    }
+    ++counts[g];
+    b->group.push_back(g);
+  }
+  // launch choice per group: tuned for its size when a tune cache is given; otherwise the
+  // shape's single-problem plan, with the block exchange over distributed shared memory
+  // (one CTA per SM) while every group's clusters fit on the GPU at once, else through L2
+  // (two clusters share an SM group)
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess || sms <= 0) sms = 1;
+  int ctas = 0;
+  for (size_t g = 0; g < keys.size(); ++g) {
+    int C, bb, rp, cp;
+    bkfac::jacobi_plan(keys[g].rows, keys[g].cols, (bkfac::DType)keys[g].jt, &C, &bb, &rp, &cp);
+    ctas += C * counts[g];
+  }
+  // clusters of 16 do not pack every SM (they must sit in one GPU processing cluster)
+  const bool all_at_once = ctas <= sms - sms / 16;
+  b->choice.assign(keys.size(), bkfac::JacobiChoice{});
+  for (size_t g = 0; g < keys.size(); ++g) {
+    bkfac::JacobiChoice c;
+    if (tune_cache && bkfac::tune_group(keys[g].rows, keys[g].cols, (bkfac::DType)keys[g].jt, counts[g], &c) ==
+                          BKFAC_OK) {
+      b->choice[g] = c;
+      continue;
+    }
+    int bt = 0, dsm = 1;
+    if (bkfac::tune_lookup(keys[g].rows, keys[g].cols, (bkfac::DType)keys[g].jt, &bt, &dsm)) c.b_max = bt;
+    c.dsm = all_at_once ? dsm : 0;
+    b->choice[g] = c;
+  }
+  if (tune_cache) bkfac::tune_save(tune_cache);
   return b;
 }
 

@@ -815,13 +815,13 @@ bool chol_block_ok(int n) { return n >= 32 && chol_block_smem(n) <= 200 * 1024; 
 int launch_chol_block(const double* Gm, int n, double* R, double thr_rel, const double* scale, double near_tol,
                       int* near_out, double neg_rel, cudaStream_t s) {
   if (!chol_block_ok(n)) return (int)cudaErrorInvalidValue;
-  static std::atomic<int> configured{0};
-  if (!configured.load()) {
+  static std::atomic<uint64_t> configured{0};
+  if (!configured_here(configured)) {
     cudaError_t e = cudaFuncSetAttribute(chol_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(chol_block_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return (int)e;
-    configured.store(1);
+    mark_configured(configured);
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(16, 1, 1);
@@ -855,14 +855,14 @@ bool chol_core_ok(int n, int rows_pad, int cols_pad) {
 namespace {
 template <typename TK, bool RM>
 int launch_core_typed(const CoreCholArgs& a, cudaStream_t s) {
-  static std::atomic<int> configured{0};  // attributes set once (the call can stall the host)
-  if (!configured.load()) {
+  static std::atomic<uint64_t> configured{0};  // attributes set once (the call can stall the host)
+  if (!configured_here(configured)) {
     cudaError_t e =
         cudaFuncSetAttribute(chol_core_kernel<TK, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(chol_core_kernel<TK, RM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return (int)e;
-    configured.store(1);
+    mark_configured(configured);
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(16, 1, 1);
@@ -934,13 +934,13 @@ int launch_chol_cluster(const double* Gm, int n, double* R, double thr_rel, cons
   if (C == 0) return (int)cudaErrorInvalidValue;
   const int w = (n + C - 1) / C;
   const size_t smem = (size_t)2 * n * w * sizeof(double);
-  static std::atomic<int> configured{0};  // attributes set once (the call can stall the host)
-  if (!configured.load()) {
+  static std::atomic<uint64_t> configured{0};  // attributes set once (the call can stall the host)
+  if (!configured_here(configured)) {
     cudaError_t e = cudaFuncSetAttribute(chol_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(chol_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return (int)e;
-    configured.store(1);
+    mark_configured(configured);
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)C, 1, 1);

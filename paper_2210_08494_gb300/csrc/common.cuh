@@ -1,6 +1,8 @@
 // common.cuh -- shared definitions of libbkfac (GB300, sm_103a).
 #pragma once
 
+#include <atomic>
+
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -91,6 +93,24 @@ struct GemmArgs {
 
 enum DType { DT_F64 = 0, DT_F32 = 1 };
 
+// Function attributes (shared-memory size, cluster size) are per device: a set of
+// per-device bits records where a kernel's attributes were set (devices 0..63).
+inline int current_device_bit() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  return dev;
+}
+inline bool configured_here(const std::atomic<uint64_t>& mask) {
+  return (mask.load(std::memory_order_acquire) >> current_device_bit()) & 1u;
+}
+inline void mark_configured(std::atomic<uint64_t>& mask) {
+  mask.fetch_or(uint64_t(1) << current_device_bit(), std::memory_order_release);
+}
+
+// streaming multiprocessors of the current device (queried once per device and
+// cached; the split-K and grid-size heuristics size their work to it)
+int sm_count();
+
 // launchers implemented in gemm.cu; return a cudaError_t
 // in_t: element type of A/B; acc_t: accumulator; out_t: C/D element type
 // (the number of kernels launched is added to the launch counter)
@@ -106,6 +126,22 @@ int gemm_pick_splits(int M, int N, int K, int sm_count);
 int tc_gemm_run(const GemmArgs& g, cudaStream_t s);
 bool tc_gemm_enabled();
 int splitk_reduce_f32(const GemmArgs& g, cudaStream_t s);
+// TMA-fed tensor-core product of BF16 K-major operands (tma_gemm.cu):
+// C (M x N) = alpha sum_k A[m, k] B[n, k] + the epilogue of g (g.M, g.N, g.C, g.ldc,
+// g.c_rowmaj, alpha, beta / beta_dev, rs, cs, ds, D, ldd; split K into g.partial);
+// A is M x K with row pitch lda, B is N x K with row pitch ldb (elements, multiples
+// of 8; 16-byte aligned bases)
+bool tma_gemm_available();
+int64_t bf16_ld(int k);  // row pitch (elements) of a BF16 K-major copy with k columns
+int tma_gemm_run(const void* A, int64_t lda, const void* B, int64_t ldb, int K, const GemmArgs& g, cudaStream_t s);
+// FP32 -> BF16 (round to nearest even) copies: G (R x C row-major) and its transpose;
+// k columns of length d (same layout); [X0 | X1] (dim x (k0 + k1) column-major) as a
+// dim x (k0 + k1) row-major matrix
+int launch_cvt_both(const float* G, int64_t ldg, int R, int C, void* Gb, int64_t ldb, void* Gt, int64_t ldt,
+                    cudaStream_t s);
+int launch_cvt_cols(const float* X, int64_t ld, int d, int k, void* Y, int64_t ldo, cudaStream_t s);
+int launch_cvt_cat_t(const float* X0, int64_t ld0, int k0, const float* X1, int64_t ld1, int k1, int dim, void* Y,
+                     int64_t ldy, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Small dense kernels (small.cu)
@@ -211,9 +247,6 @@ struct JacobiBatch {
 };
 // probs: host array of nprob <= kMaxJacobiProblems problems sharing the cluster size C
 // (passed by value as a kernel parameter, so the launch can be captured in a graph)
-// while set (per host thread), launch_jacobi prefers the L2 block exchange: many
-// eigensolves are about to run concurrently (batch API)
-void jacobi_set_many_concurrent(bool on);
 int launch_jacobi(const JacobiProblem* probs, int nprob, int C, DType j_t, double tol, int max_sweeps,
                   cudaStream_t s);
 // explicit block-exchange mode (false: through L2, true: distributed shared memory)
@@ -227,6 +260,34 @@ int tune_load(const char* path);
 int tune_save(const char* path);
 // shared memory bytes one CTA needs for a problem
 size_t jacobi_smem_bytes(int b, int rows_pad, DType j_t);
+// A caller's choice of the eigensolve's launch shape: the block-width cap (0: the
+// shape's tuned or default plan) and the block exchange (-1: the default, 0: through
+// L2, 1: over distributed shared memory).
+struct JacobiChoice {
+  int b_max = 0;
+  int dsm = -1;
+};
+// An update enqueued up to its eigensolve (api.cu): the eigensolve's problem, its
+// cluster size, precision and stopping tolerance.
+struct StagedEig {
+  JacobiProblem jp;
+  int C = 0;
+  DType jt = DT_F32;
+  double tol = 0.0;
+};
+// bkfac_init (init) / bkfac_update split at the eigensolve, for a batch that runs the
+// eigensolves of many factors as grouped launches: update_stage_pre enqueues
+// everything before it, update_stage_post (same arguments, after the eigensolve ran
+// on the stream) everything after it and advances r_cur and step.
+int update_stage_pre(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, bool init, void* ws,
+                     size_t ws_bytes, const JacobiChoice* jc, cudaStream_t s, StagedEig* out);
+int update_stage_post(bkfac_factor* f, const void* X, int64_t ldx, int n, double rho, bool init, void* ws,
+                      size_t ws_bytes, const JacobiChoice* jc, cudaStream_t s);
+int eig_sweep_cap();
+// the tuned choice for a grouped launch of `count` same-shape eigensolves (tune.cu):
+// lookup only, or timing the candidates when the table has no entry
+bool tune_group_lookup(int rows, int cols, DType jt, int count, JacobiChoice* out);
+int tune_group(int rows, int cols, DType jt, int count, JacobiChoice* out);
 // self-test of the bounded mbarrier wait (jacobi.cu): a wait on a phase nothing
 // completes gives up after limit_cycles and records BKFAC_ETIMEOUT; *out (may be
 // null) receives 1 on time-out

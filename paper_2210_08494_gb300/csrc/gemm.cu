@@ -609,7 +609,7 @@ int run_typed(const GemmArgs& g, cudaStream_t s) {
 int gemm_pick_splits(int M, int N, int K, int /*sm_count*/) {
   // a fixed CTA target keeps workspace sizes independent of the device
   const int64_t tiles = ceil_div(M, BM) * ceil_div(N, BN);
-  const int64_t target = 2 * 152;
+  const int64_t target = 2 * sm_count();
   int64_t s = std::max<int64_t>(1, target / std::max<int64_t>(tiles, 1));
   s = std::min<int64_t>(s, std::max<int64_t>(1, K / 256));
   s = std::min<int64_t>(s, 32);
@@ -653,7 +653,7 @@ int gemm_run(const GemmArgs& g, DType in_t, DType acc_t, DType out_t, cudaStream
       GemmArgs a = g;
       const int64_t tiles = ceil_div(g.M, LBM) * ceil_div(g.N, LBN);
       const int64_t room = a.partial ? (int64_t)(a.partial_bytes / ((size_t)g.M * g.N * sizeof(float))) : 0;
-      if (a.splits <= 1 && tiles < 152 && room >= 2)
+      if (a.splits <= 1 && tiles < sm_count() && room >= 2)
         a.splits = (int)std::min<int64_t>(std::min<int64_t>(4, 304 / tiles), room);
       if (a.splits > 1 && room < a.splits) a.splits = (int)std::max<int64_t>(1, room);
       return run_large_f32(a, s);
@@ -666,7 +666,7 @@ int gemm_run(const GemmArgs& g, DType in_t, DType acc_t, DType out_t, cudaStream
       const int64_t tiles = ceil_div(g.M, LBM) * ceil_div(g.N, LBN);
       const int64_t room = (int64_t)(g.partial_bytes / ((size_t)g.M * g.N * sizeof(float)));
       const int64_t sp = std::min<int64_t>(std::min<int64_t>(room, 32),
-                                           std::min<int64_t>(K / 128, ceil_div(2 * 152, tiles)));
+                                           std::min<int64_t>(K / 128, ceil_div(2 * sm_count(), tiles)));
       if (sp >= 8) {
         GemmArgs a = g;
         a.splits = (int)sp;

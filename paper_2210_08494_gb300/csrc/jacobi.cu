@@ -785,14 +785,14 @@ int launch_typed(const JacobiBatch& batch, int nprob, int C, int b, size_t smem,
     return (int)cudaErrorInvalidValue;
   auto kfn = jacobi_kernel<J, NV, DSM>;
   // function attributes are set once per instantiation (the call can stall the host)
-  static std::atomic<int> configured{0};
+  static std::atomic<uint64_t> configured{0};
   cudaError_t e = cudaSuccess;
-  if (!configured.load()) {
+  if (!configured_here(configured)) {
     e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return (int)e;
-    configured.store(1);
+    mark_configured(configured);
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nprob * C), 1, 1);
@@ -871,20 +871,14 @@ void jacobi_plan(int rows, int cols, DType j_t, int* C_out, int* b_out, int* row
   jacobi_plan_with(rows, cols, j_t, b_max, C_out, b_out, rows_pad, cols_pad);
 }
 
-namespace {
-thread_local bool t_many_concurrent = false;
-}
-
-void jacobi_set_many_concurrent(bool on) { t_many_concurrent = on; }
-
 int launch_jacobi(const JacobiProblem* probs, int nprob, int C, DType j_t, double tol, int max_sweeps,
                   cudaStream_t s) {
   // Block exchange over distributed shared memory (three buffers per CTA, one CTA
-  // per SM) unless the tuning table says otherwise.  While a batch enqueues more
-  // eigensolves than one-CTA-per-SM clusters fit on the GPU, the exchange goes
-  // through L2 instead: a third of the shared memory lets two clusters share SMs.
-  int b = 0, dsm = t_many_concurrent ? 0 : 1;
-  if (nprob > 0 && !t_many_concurrent) tune_lookup(probs[0].rows, probs[0].cols, j_t, &b, &dsm);
+  // per SM) unless the tuning table says otherwise.  (A batch that runs more
+  // eigensolves than such clusters fit on the GPU picks the L2 exchange for its
+  // grouped launches, where a third of the shared memory lets two clusters share SMs.)
+  int b = 0, dsm = 1;
+  if (nprob > 0) tune_lookup(probs[0].rows, probs[0].cols, j_t, &b, &dsm);
   return launch_jacobi_mode(probs, nprob, C, j_t, tol, max_sweeps, dsm != 0, s);
 }
 

@@ -592,11 +592,11 @@ int launch_chol(const double* Gm, int n, double* R, double thr_rel, const double
 
 template <typename T>
 void trinv_launch(const double* R, int n, T* Rinv, cudaStream_t s) {
-  static std::atomic<int> configured{0};  // attribute set once (the call can stall the host)
-  if (!configured.load()) {
+  static std::atomic<uint64_t> configured{0};  // attribute set once (the call can stall the host)
+  if (!configured_here(configured)) {
     cudaFuncSetAttribute(trinv_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(trinv_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    configured.store(1);
+    mark_configured(configured);
   }
   const int blocks = (int)ceil_div(n, 32);
   const size_t xs = (size_t)32 * n * sizeof(T) + (size_t)n * sizeof(T);
@@ -609,10 +609,10 @@ void trinv_launch(const double* R, int n, T* Rinv, cudaStream_t s) {
 
 template <typename T>
 void trinv_blocked_launch(const double* R, int n, T* Rinv, const int* near, cudaStream_t s) {
-  static std::atomic<int> configured{0};  // attribute set once (the call can stall the host)
-  if (!configured.load()) {
+  static std::atomic<uint64_t> configured{0};  // attribute set once (the call can stall the host)
+  if (!configured_here(configured)) {
     cudaFuncSetAttribute(trinv_blocked_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    configured.store(1);
+    mark_configured(configured);
   }
   const int nb = (int)ceil_div(n, 32);
   const size_t smem = (size_t)3 * nb * 1024 * sizeof(T);

@@ -567,19 +567,19 @@ int tc_launch(const GemmArgs& g, cudaStream_t s) {
   const int64_t tiles = ceil_div(a.M, TM) * ceil_div(a.N, TN);
   // split K so that about two CTAs per SM are busy, within the partial buffer
   int64_t splits = 1;
-  if (a.partial != nullptr && tiles < 2 * 152 && K > 4 * Md::TK) {
+  if (a.partial != nullptr && tiles < 2 * sm_count() && K > 4 * Md::TK) {
     const int64_t room = (int64_t)(a.partial_bytes / ((size_t)a.M * a.N * sizeof(float)));
-    splits = std::min<int64_t>(std::min<int64_t>(ceil_div(2 * 152, tiles), (int64_t)K / (2 * Md::TK)), room);
+    splits = std::min<int64_t>(std::min<int64_t>(ceil_div(2 * sm_count(), tiles), (int64_t)K / (2 * Md::TK)), room);
     splits = std::max<int64_t>(1, std::min<int64_t>(splits, 32));
   }
   a.k_chunk = (int)round_up(ceil_div(std::max(K, 1), splits), Md::TK);
   a.splits = (int)std::max<int64_t>(1, ceil_div(std::max(K, 1), a.k_chunk));
-  static std::atomic<int> configured{0};  // attribute set once (the call can stall the host)
-  if (!configured.load()) {
+  static std::atomic<uint64_t> configured{0};  // attribute set once (the call can stall the host)
+  if (!configured_here(configured)) {
     const cudaError_t e =
         cudaFuncSetAttribute(tc_gemm_kernel<X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Md::SMEM_BYTES);
     if (e != cudaSuccess) return (int)e;
-    configured.store(1);
+    mark_configured(configured);
   }
   dim3 grid((unsigned)ceil_div(a.N, TN), (unsigned)ceil_div(a.M, TM), (unsigned)a.splits);
   tc_gemm_kernel<X3><<<grid, TC_THREADS, Md::SMEM_BYTES, s>>>(a);

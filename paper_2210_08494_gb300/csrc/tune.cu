@@ -3,10 +3,15 @@
 // exchange between rounds (through L2 or over distributed shared memory), by
 // timing every candidate on a synthetic core of that shape: a Brand-like factor
 // L = [[diag(sqrt(rho sigma)), sqrt(c) M], [0, sqrt(c) R]] with a power-law sigma
-// and Gaussian M, upper-triangular R.  Results live in a process-wide table
-// keyed by (rows, cols, precision) and can be saved to / loaded from a text
-// file ("rows cols prec b dsm ms" per line).  The table only changes launch
-// shapes; every candidate computes the same decomposition.
+// and Gaussian M, upper-triangular R.  A second table holds the choice for a
+// batch's grouped launch of `count` same-shape eigensolves, timed on `count`
+// copies of the synthetic core in one launch: wider blocks on smaller clusters,
+// or the L2 exchange (a third of the shared memory, two clusters per SM group),
+// let more problems run at once, at a cost per problem.  Results live in
+// process-wide tables keyed by (rows, cols, precision[, count]) and can be
+// saved to / loaded from a text file ("rows cols prec b dsm ms" per line for a
+// single problem, "G rows cols prec count b dsm ms" for a group).  The tables
+// only change launch shapes; every candidate computes the same decomposition.
 #include <cmath>
 #include <cstdio>
 #include <map>
@@ -27,8 +32,18 @@ struct TuneEntry {
 };
 std::mutex g_tmu;
 std::map<std::tuple<int, int, int>, TuneEntry> g_table;
+std::map<std::tuple<int, int, int, int>, TuneEntry> g_group_table;
 
 }  // namespace
+
+bool tune_group_lookup(int rows, int cols, DType jt, int count, JacobiChoice* out) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  auto it = g_group_table.find(std::make_tuple(rows, cols, (int)jt, count));
+  if (it == g_group_table.end()) return false;
+  out->b_max = it->second.b;
+  out->dsm = it->second.dsm;
+  return true;
+}
 
 bool tune_lookup(int rows, int cols, DType jt, int* b, int* dsm) {
   std::lock_guard<std::mutex> lk(g_tmu);
@@ -50,12 +65,22 @@ int load_file(const char* path) {
   if (!path) return 0;
   FILE* f = std::fopen(path, "r");
   if (!f) return 0;
-  int rows, cols, prec, b, dsm, n = 0;
+  int rows, cols, prec, b, dsm, count, n = 0;
   float ms;
-  while (std::fscanf(f, "%d %d %d %d %d %f", &rows, &cols, &prec, &b, &dsm, &ms) == 6) {
-    if (b >= 2 && b <= 32 && (b % 2) == 0 && (prec == 0 || prec == 1)) {
-      put(rows, cols, (DType)prec, TuneEntry{b, dsm ? 1 : 0, ms});
-      ++n;
+  char line[256];
+  while (std::fgets(line, sizeof line, f)) {
+    if (line[0] == 'G') {
+      if (std::sscanf(line + 1, "%d %d %d %d %d %d %f", &rows, &cols, &prec, &count, &b, &dsm, &ms) == 7 &&
+          b >= 2 && b <= 32 && (b % 2) == 0 && (prec == 0 || prec == 1) && count >= 1) {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        g_group_table[std::make_tuple(rows, cols, prec, count)] = TuneEntry{b, dsm ? 1 : 0, ms};
+        ++n;
+      }
+    } else if (std::sscanf(line, "%d %d %d %d %d %f", &rows, &cols, &prec, &b, &dsm, &ms) == 6) {
+      if (b >= 2 && b <= 32 && (b % 2) == 0 && (prec == 0 || prec == 1)) {
+        put(rows, cols, (DType)prec, TuneEntry{b, dsm ? 1 : 0, ms});
+        ++n;
+      }
     }
   }
   std::fclose(f);
@@ -70,15 +95,20 @@ int save_file(const char* path) {
   for (const auto& kv : g_table)
     std::fprintf(f, "%d %d %d %d %d %.4f\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
                  kv.second.b, kv.second.dsm, kv.second.ms);
+  for (const auto& kv : g_group_table)
+    std::fprintf(f, "G %d %d %d %d %d %d %.4f\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                 std::get<2>(kv.first), std::get<3>(kv.first), kv.second.b, kv.second.dsm, kv.second.ms);
   std::fclose(f);
   return BKFAC_OK;
 }
 
-// time one candidate: copy the synthetic core in, run the Jacobi, return ms (-1 on failure)
-float time_candidate(int rows, int cols, DType jt, int b, int dsm, const std::vector<double>& host_core) {
+// time one candidate: copy `count` copies of the synthetic core in, run them as one
+// grouped Jacobi launch, return ms (-1 on failure)
+float time_candidate(int rows, int cols, DType jt, int b, int dsm, const std::vector<double>& host_core,
+                     int count = 1) {
   int C, bb, rp, cp;
   jacobi_plan_with(rows, cols, jt, b, &C, &bb, &rp, &cp);
-  if (jacobi_smem_bytes(bb, rp, jt) > 200 * 1024) return -1.f;
+  if (jacobi_smem_bytes(bb, rp, jt) > 200 * 1024 || count < 1 || count > kMaxJacobiProblems) return -1.f;
   const size_t es = jt == DT_F64 ? 8 : 4;
   void* W = nullptr;
   double* cn = nullptr;
@@ -86,8 +116,9 @@ float time_candidate(int rows, int cols, DType jt, int b, int dsm, const std::ve
   int* sw = nullptr;
   float ms = -1.f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaMalloc(&W, (size_t)rp * cp * es) != cudaSuccess || cudaMalloc(&cn, (size_t)cp * 8) != cudaSuccess ||
-      cudaMalloc(&stamp, (size_t)cp * 4) != cudaSuccess || cudaMalloc(&sw, 256) != cudaSuccess)
+  if (cudaMalloc(&W, (size_t)count * rp * cp * es) != cudaSuccess ||
+      cudaMalloc(&cn, (size_t)cp * 8) != cudaSuccess || cudaMalloc(&stamp, (size_t)count * cp * 4) != cudaSuccess ||
+      cudaMalloc(&sw, (size_t)count * 256) != cudaSuccess)
     goto out;
   {
     // host matrix (rows x cols, column-major) -> padded device layout in the Jacobi type
@@ -105,22 +136,27 @@ float time_candidate(int rows, int cols, DType jt, int b, int dsm, const std::ve
     cudaMemcpy(cn, norms.data(), (size_t)cp * 8, cudaMemcpyHostToDevice);
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    JacobiProblem p;
-    p.W = W;
-    p.rows = rows;
-    p.rows_pad = rp;
-    p.cols_pad = cp;
-    p.b = bb;
-    p.colnorm2 = cn;
-    p.sweeps_out = sw;
-    p.stamp = stamp;
+    std::vector<JacobiProblem> ps(count);
+    for (int q = 0; q < count; ++q) {
+      JacobiProblem& p = ps[q];
+      p.W = (char*)W + (size_t)q * rp * cp * es;
+      p.rows = rows;
+      p.cols = cols;
+      p.rows_pad = rp;
+      p.cols_pad = cp;
+      p.b = bb;
+      p.colnorm2 = cn;
+      p.sweeps_out = sw + 64 * q;
+      p.stamp = stamp + (size_t)q * cp;
+    }
     const double u = jt == DT_F64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
     const double tol = std::max(4.0 * std::sqrt((double)rows), 32.0) * u;
     float best = -1.f;
     for (int rep = 0; rep < 2; ++rep) {
-      cudaMemcpy(W, buf.data(), buf.size(), cudaMemcpyHostToDevice);
+      for (int q = 0; q < count; ++q)
+        cudaMemcpy((char*)W + (size_t)q * rp * cp * es, buf.data(), buf.size(), cudaMemcpyHostToDevice);
       cudaEventRecord(e0, 0);
-      const int rc = launch_jacobi_mode(&p, 1, C, jt, tol, 40, dsm != 0, 0);
+      const int rc = launch_jacobi_mode(ps.data(), count, C, jt, tol, 40, dsm != 0, 0);
       cudaEventRecord(e1, 0);
       if (rc != 0 || cudaEventSynchronize(e1) != cudaSuccess) goto out;
       float t = 0.f;
@@ -142,11 +178,9 @@ out:
 
 }  // namespace
 
-// tune the Jacobi of an N x N Brand core (rows = cols = N) or a dense-path factor
-int tune_shape(int rows, int cols, DType jt) {
-  int b0, d0;
-  if (tune_lookup(rows, cols, jt, &b0, &d0)) return BKFAC_OK;
-  // synthetic core: power-law diagonal block plus Gaussian update columns
+// synthetic core of an eigensolve shape: power-law diagonal block plus Gaussian
+// update columns
+static std::vector<double> synthetic_core(int rows, int cols) {
   std::mt19937_64 rng(12345u + (unsigned)rows * 7919u + (unsigned)cols);
   std::normal_distribution<double> nd(0.0, 1.0);
   const int k = cols > rows ? 0 : std::max(0, cols / 2);
@@ -158,6 +192,14 @@ int tune_shape(int rows, int cols, DType jt) {
       const bool upper_tri = i >= k && (i - k) > (j - k);
       core[(size_t)i + (size_t)j * rows] = upper_tri ? 0.0 : std::sqrt(c) * nd(rng) * std::pow(i + 1.0, -0.6);
     }
+  return core;
+}
+
+// tune the Jacobi of an N x N Brand core (rows = cols = N) or a dense-path factor
+int tune_shape(int rows, int cols, DType jt) {
+  int b0, d0;
+  if (tune_lookup(rows, cols, jt, &b0, &d0)) return BKFAC_OK;
+  const std::vector<double> core = synthetic_core(rows, cols);
   float best = 1e30f;
   TuneEntry pick{16, 0, -1.f};
   for (int b : {8, 16}) {
@@ -171,6 +213,33 @@ int tune_shape(int rows, int cols, DType jt) {
   }
   if (pick.ms < 0.f) return BKFAC_ECUDA;
   put(rows, cols, jt, pick);
+  return BKFAC_OK;
+}
+
+// tune a batch's grouped launch of `count` eigensolves of one shape: block-width
+// caps 8, 16 and 32 (cluster sizes down to 8) with either block exchange
+int tune_group(int rows, int cols, DType jt, int count, JacobiChoice* out) {
+  if (tune_group_lookup(rows, cols, jt, count, out)) return BKFAC_OK;
+  count = std::min(std::max(count, 1), kMaxJacobiProblems);
+  const std::vector<double> core = synthetic_core(rows, cols);
+  float best = 1e30f;
+  TuneEntry pick{16, 0, -1.f};
+  for (int b : {8, 16, 32}) {
+    for (int dsm : {0, 1}) {
+      const float t = time_candidate(rows, cols, jt, b, dsm, core, count);
+      if (t > 0.f && t < best) {
+        best = t;
+        pick = TuneEntry{b, dsm, t};
+      }
+    }
+  }
+  if (pick.ms < 0.f) return BKFAC_ECUDA;
+  {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_group_table[std::make_tuple(rows, cols, (int)jt, count)] = pick;
+  }
+  out->b_max = pick.b;
+  out->dsm = pick.dsm;
   return BKFAC_OK;
 }
 

@@ -2,8 +2,10 @@
 
 The preconditioning work partitions into independent layers: a layer's two
 factor updates and its apply need nothing from other layers.  So ranks take
-whole layers -- no data-path collective -- and the only communication is for
-timing (a barrier and the max of the elapsed times over ranks).
+whole layers, and the one data exchange of a step comes after the work: every
+rank needs every layer's preconditioned gradient S_l for its weight update, so
+the ranks all-gather the steps of their layers (exchange_steps).  Timing takes
+the max of the elapsed times over ranks.
 
 The per-layer cost model follows the update's work: d (r + n)^2 for the
 tall-skinny products plus a (r + n)^3 term for the core eigensolve, for each
@@ -47,3 +49,46 @@ def max_over_ranks(value: float, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def owners(parts):
+    """Layer index -> owning rank for an assignment from assign_layers."""
+    own = {}
+    for r, p in enumerate(parts):
+        for l in p:
+            own[l] = r
+    return own
+
+
+def exchange_steps(S, parts, rank: int):
+    """All-gather of the preconditioned gradients: rank `rank` has written S[l] for its
+    layers parts[rank]; afterwards every rank holds every S[l] (written in place).
+
+    One collective per step: each rank packs its layers' steps, in layer order, into one
+    flat buffer of the largest rank's size, the buffers are all-gathered, and each rank
+    unpacks the other ranks' layers.  S[l] may be a strided 2-D view (padded rows)."""
+    import torch
+    import torch.distributed as dist
+
+    world = len(parts)
+    if world == 1:
+        return
+    sizes = [sum(S[l].numel() for l in p) for p in parts]
+    m = max(sizes)
+    ref = S[parts[rank][0]] if parts[rank] else S[0]
+    buf = torch.zeros(m, dtype=ref.dtype, device=ref.device)
+    off = 0
+    for l in parts[rank]:
+        k = S[l].numel()
+        buf[off:off + k].view(S[l].shape).copy_(S[l])
+        off += k
+    out = torch.empty(world * m, dtype=ref.dtype, device=ref.device)
+    dist.all_gather_into_tensor(out, buf)
+    for r, p in enumerate(parts):
+        if r == rank:
+            continue
+        off = r * m
+        for l in p:
+            k = S[l].numel()
+            S[l].copy_(out[off:off + k].view(S[l].shape))
+            off += k

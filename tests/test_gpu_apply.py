@@ -99,3 +99,35 @@ def test_apply_wide_layer_tf32x3(oracle):
     """The wide layer's apply with 3xTF32 tensor-core passes."""
     err = run_apply(oracle, 4097, 256, 256, 4096, 256, 256, bkfac.F32, lamA=1e-2, lamG=1e-2, fflags=bkfac.FLAG_TF32X3)
     print(f"wide-layer 3xTF32 apply relative error {err:.2e}")
+
+
+@pytest.mark.parametrize("dA,kA,dG,kG", [(301, 24, 130, 16), (1000, 64, 777, 48), (129, 0, 200, 10), (257, 9, 70, 0),
+                                          (96, 0, 40, 0), (600, 200, 450, 130)])
+def test_apply_mixed_shapes(oracle, dA, kA, dG, kG):
+    """The mixed path's apply (BF16 operands rounded once into K-major copies, products on
+    the TMA-fed tensor cores): ragged tiles along every dimension, empty factors, ranks
+    above one tile; relative Frobenius and element-wise against the oracle."""
+    err = run_apply(oracle, dA, max(kA, 1), kA, dG, max(kG, 1), kG, bkfac.MIXED_BF16, seed=11)
+    print(f"mixed apply {dG} x {dA} (kA {kA}, kG {kG}): {err:.2e}")
+
+
+def test_apply_mixed_in_place(oracle):
+    run_apply(oracle, 333, 20, 20, 190, 12, 12, bkfac.MIXED_BF16, inplace=True, seed=13)
+
+
+def test_apply_wide_layer_mixed(oracle):
+    """The wide layer (G 4096 x 4097, r = 256 on both sides) on the mixed path, element by element."""
+    fA, UA, sA = make_factor(4097, 256, 256, bkfac.MIXED_BF16, 21)
+    fG, UG, sG = make_factor(4096, 256, 256, bkfac.MIXED_BF16, 22)
+    Gn = synth.gradient(4096, 4097, 23, 0)
+    G = bkfac.grad_tensor(4096, 4097, torch.float32)
+    G.copy_(torch.from_numpy(Gn))
+    S = bkfac.grad_tensor(4096, 4097, torch.float32)
+    bkfac.bkfac_apply(fA, fG, 1e-2, 1e-2, G, S)
+    assert bkfac.bkfac_status() == bkfac.OK
+    So = oracle.apply(UA, sA, 1e-2, UG, sG, 1e-2, G.double().cpu().numpy())
+    Sg = S.double().cpu().numpy()
+    err = rel(Sg, So)
+    em = float(np.abs(Sg - So).max() / np.abs(So).max())
+    print(f"wide-layer mixed apply: {err:.2e} (element-wise {em:.2e})")
+    assert err < 1e-2 and em < 1e-2

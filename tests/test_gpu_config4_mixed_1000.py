@@ -33,7 +33,7 @@ from paper_2210_08494_gb300 import bkfac, synth
 from tests import oracle_worker
 from tests.parity_util import judge_step, lowrank_rel_err, max_sin_theta, rel
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(900)]
 
 SHAPES = [(513, 1024), (1025, 2048), (2049, 4096), (4097, 4096), (4097, 10)]
 RANKS = [64, 128, 256]
@@ -62,7 +62,7 @@ def test_config4_mixed_1000_steps_against_fp64_oracle(oracle):
     threads = max(1, (os.cpu_count() or 2) // 2)
     r0 = layer_shape(0)[2]
     # oracle trajectories of layer 0's A and Gamma, beside the GPU loop
-    workers = [oracle_worker.start(r0, RHO, EVERY, threads) for _ in range(2)]
+    workers = [oracle_worker.Worker(r0, RHO, EVERY, threads) for _ in range(2)]
     dev = torch.device("cuda")
     gens = [(synth.DevicePowerlaw(layer_shape(l)[0], ALPHA, 4000 + 10 * l, dev),
              synth.DevicePowerlaw(layer_shape(l)[1], ALPHA, 4001 + 10 * l, dev)) for l in range(NL)]
@@ -85,7 +85,6 @@ def test_config4_mixed_1000_steps_against_fp64_oracle(oracle):
         batch = bkfac.Batch(layers, N, bkfac.MIXED_BF16)
         S = [bkfac.grad_tensor(g.shape[0], g.shape[1], torch.float32) for g in G]
         runs[name] = {"layers": layers, "batch": batch, "S": S, "snaps": {}, "ms": 0.0}
-    results = [[], []]
     stream = torch.cuda.Stream()
     try:
         for t in range(STEPS):
@@ -94,11 +93,9 @@ def test_config4_mixed_1000_steps_against_fp64_oracle(oracle):
                     gens[l][0].draw(XA[l], N, t)
                     gens[l][1].draw(XG[l], N, t)
             stream.synchronize()
-            for w, (proc, conn) in enumerate(workers):
+            for w, wk in enumerate(workers):
                 X = (XA if w == 0 else XG)[0]
-                conn.send((t, X[:, : layer_shape(0)[w]].double().cpu().numpy()))
-                while conn.poll():
-                    results[w].append(conn.recv())
+                wk.send(t, X[:, : layer_shape(0)[w]].double().cpu().numpy())
             last = t + 1 == STEPS
             for name, run in runs.items():
                 b = run["batch"]
@@ -126,15 +123,10 @@ def test_config4_mixed_1000_steps_against_fp64_oracle(oracle):
                     a, g = run["layers"][0]
                     run["snaps"][t] = tuple(x.double().cpu().numpy() for f in (a, g) for x in f.state()) + (
                         run["S"][0].double().cpu().numpy(),)
-        for w, (proc, conn) in enumerate(workers):
-            conn.send(None)
-            while len(results[w]) < STEPS // EVERY:
-                results[w].append(conn.recv())
-            proc.join(timeout=60)
+        results = [wk.finish() for wk in workers]
     finally:
-        for proc, conn in workers:
-            if proc.is_alive():
-                proc.kill()
+        for wk in workers:
+            wk.kill()
     ref = {t: (UA, sA, UG, sG) for (t, UA, sA), (_, UG, sG) in zip(results[0], results[1])}
     k4 = max(1, r0 // 4)
     for name, run in runs.items():

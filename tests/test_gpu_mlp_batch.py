@@ -20,7 +20,7 @@ import torch
 from paper_2210_08494_gb300 import bkfac, synth
 from tests.parity_util import judge_step, rel
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(900)]
 
 WIDTHS = [4096] * 8 + [10]
 R, N, RHO, LAM = 220, 256, 0.95, 1e-2

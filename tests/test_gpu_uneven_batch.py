@@ -24,7 +24,7 @@ import torch
 from paper_2210_08494_gb300 import bkfac, synth
 from tests.parity_util import judge_step, orth_err, rel
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(900)]
 
 SHAPES = [(513, 1024), (1025, 2048), (2049, 4096), (4097, 4096), (4097, 10)]
 RANKS = [64, 128, 256]
@@ -110,7 +110,7 @@ def test_uneven_batch_graph_step_matches_oracle(oracle, inputs, dtype):
     assert st == bkfac.OK, bkfac.strerror(st)
     batch.sync_descriptors()
     tol = TOL[dtype]
-    report = []
+    report, failures = [], []
     for l in SAMPLED:
         dA, dG, r = layer_shape(l)
         post = []
@@ -128,10 +128,14 @@ def test_uneven_batch_graph_step_matches_oracle(oracle, inputs, dtype):
             # U' = [U Q] V is an FP32 product over K = r + n <= 384 terms: its departure
             # from orthonormality is O(K u_f32) = 2.3e-5 per step on top of the
             # Jacobi tolerance; 1e-4 is the FP32 path's tolerance
-            m = judge_step(Ug, sg, Uo[: info["r_new"]], so[: info["r_new"]], k, dtype, tol,
-                           orth_tol=1e-4 if dtype == bkfac.F32 else 2e-2)
-            report.append("layer %d %s d=%d r=%d: sigma %.2e per-mode %.2e reconstruction %.2e%s"
-                          % (l, "AG"[w], d, f.r, m["sigma"], m["mode"], m["recon"], " (near tie)" if m["tie"] else ""))
+            try:
+                m = judge_step(Ug, sg, Uo[: info["r_new"]], so[: info["r_new"]], k, dtype, tol,
+                               orth_tol=1e-4 if dtype == bkfac.F32 else 2e-2)
+                report.append("layer %d %s d=%d r=%d: sigma %.2e per-mode %.2e reconstruction %.2e%s"
+                              % (l, "AG"[w], d, f.r, m["sigma"], m["mode"], m["recon"],
+                                 " (near tie)" if m["tie"] else ""))
+            except AssertionError as e:
+                failures.append(f"layer {l} {'AG'[w]} d={d}: {e}")
             post.append((Ug[:k], sg[:k]))
         (UA, sA), (UG, sG) = post
         So = oracle.apply(UA, sA, LAM, UG, sG, LAM, grads[l])
@@ -139,7 +143,8 @@ def test_uneven_batch_graph_step_matches_oracle(oracle, inputs, dtype):
         ea = rel(Sg, So)
         em = float(np.abs(Sg - So).max() / np.abs(So).max())
         report.append("layer %d apply %d x %d gradient: %.2e (elementwise %.2e)" % (l, dG, dA, ea, em))
-        assert ea < tol, (l, ea)
-        assert em < tol, (l, em)
+        if not (ea < tol and em < tol):
+            failures.append(f"layer {l} apply: {ea:.2e} / elementwise {em:.2e}")
     print("\n".join(report))
     batch.close()
+    assert not failures, failures

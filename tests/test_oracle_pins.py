@@ -583,3 +583,29 @@ def test_pins_catch_a_planted_mistake(oracle):
     K_wrong = rho * dense(Ut, sigma) + (1 - rho) * Xt.T @ Xt
     assert rel(dense(Uo, so), K_right) < 1e-13
     assert rel(dense(Uo, so), K_wrong) > 1e-2
+
+
+@pytest.mark.parametrize("case", ["steady", "init", "deficient"])
+def test_update_eigh_equals_update(oracle, case):
+    """The long-trajectory variant (LAPACK eigh for the core) is the same update:
+    eigenvalues and the represented matrix agree with the Jacobi oracle to FP64
+    rounding, including a rank-deficient residual and the first step."""
+    d, r, n = 300, 24, 20
+    rng = np.random.default_rng(31)
+    X0 = synth.powerlaw_batch(d, 32, 1.3, 77, 0)
+    U, s, info = oracle.init(X0, r)
+    k = info["r_new"]
+    X = synth.powerlaw_batch(d, n, 1.3, 77, 1)
+    if case == "init":
+        U, s, k = np.zeros((1, d)), np.zeros(1), 0
+    if case == "deficient":
+        X[10:] = X[:10]
+        X[3] = (rng.standard_normal(k) * np.sqrt(np.maximum(s[:k], 0.0))) @ U[:k]  # inside span(U)
+    Ua, sa, ia = oracle.update(U[:max(k, 1)], s[:max(k, 1)], k, X, 0.95, r)
+    Ub, sb, ib = oracle.update_eigh(U[:max(k, 1)], s[:max(k, 1)], k, X, 0.95, r)
+    assert ia["r_new"] == ib["r_new"] and ia["rank_p"] == ib["rank_p"]
+    kk = ia["r_new"]
+    assert np.abs(sa - sb).max() <= 1e-13 * sa[0]
+    Ka = (Ua[:kk].T * sa[:kk]) @ Ua[:kk]
+    Kb = (Ub[:kk].T * sb[:kk]) @ Ub[:kk]
+    assert np.linalg.norm(Ka - Kb) <= 1e-12 * np.linalg.norm(Ka)
