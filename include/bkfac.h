@@ -324,6 +324,8 @@ int bkfac_rsvd(bkfac_factor* f, const void* M, int64_t ldm, const void* Omega, i
  *     (bkfac_apply_workspace_size(fA, fG) tells how much it needs).
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     After a device reset (a new context on the device) the next call looks
+ *     it up again, so that call too must come before any capture.
  *   - All calls on a device share the one array: calls that may overlap on
  *     the GPU (different streams without ordering) race on it and give
  *     undefined results.  Order them on one stream or with events.

@@ -14,9 +14,14 @@
 // The array is a __device__ variable: every GPU that loads the library holds
 // it (BKFAC_NOALLOC_SCRATCH_BYTES) until the process exits.  In host code its
 // name is only a host-side stand-in, not a device address, so its device
-// address is looked up once per device with cudaGetSymbolAddress (with that
-// device current) and cached; that lookup happens on the first call on each
-// device.
+// address is looked up with cudaGetSymbolAddress (with the device current) on
+// the first call on each device and cached.  The cache is keyed on the device
+// and on the unique id of its current context: a device reset destroys the
+// context and the module with it, and the next call on that device looks the
+// address up again in the new context.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -28,16 +33,42 @@ static __device__ __align__(256) unsigned char g_apply_scratch[BKFAC_NOALLOC_SCR
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
-// device address of g_apply_scratch on the current device (set up on first use)
+// unique id of the calling thread's current context (0 when it cannot be read)
+unsigned long long current_context_id() {
+  static std::once_flag once;
+  static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+    cudaGetLastError();
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx) get_id(ctx, &id);
+  return id;
+}
+
+// device address of g_apply_scratch on the current device (set up on first use in
+// each context of the device)
 int scratch_address(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BKFAC_ECUDA;
+  const unsigned long long ctx = current_context_id();  // 0 before the runtime's first use
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || ctx == 0 || g_scratch_ctx[dev] != ctx) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_apply_scratch) != cudaSuccess || !p) return BKFAC_ECUDA;
     g_scratch_ptr[dev] = p;
+    g_scratch_ctx[dev] = current_context_id();  // the context the lookup ran in
   }
   *out = g_scratch_ptr[dev];
   return BKFAC_OK;

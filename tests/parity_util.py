@@ -51,8 +51,23 @@ NEAR_TIE = {0: 1e3 * 2.0 ** -53, 1: 1e3 * 2.0 ** -24, 2: 10 * 2.0 ** -8}
 
 # Per-mode eigenvalue bound relative to the largest eigenvalue (Weyl: every sorted
 # eigenvalue moves by at most the 2-norm of the perturbation, which each path's
-# rounding bounds by about N u |K|): FP64 1e-12, FP32 4e-6, mixed 8e-3 (2 u_bf16).
-MODE_TOL = {0: 1e-12, 1: 4e-6, 2: 8e-3}
+# rounding bounds by about N u |K| with N = r + n <= 512 columns): FP64 1e-12,
+# FP32 2e-5 (N u_32 = 3e-5), mixed 8e-3 (2 u_bf16, the BF16 operands of the core).
+MODE_TOL = {0: 1e-12, 1: 2e-5, 2: 8e-3}
+
+
+def mixed_apply_bound(G, S_ref, lamA, lamG, c=4.0):
+    """Stated bound of a mixed-precision inverse application: S = G / (lamA lamG) +
+    W1 U_A^T + U_G W2 adds terms of size |G| / (lamA lamG) that cancel in the span of the
+    factors, each carrying the BF16 rounding (u = 2^-8) of its operands, so the error is
+    about c u |G|_F / (lamA lamG) -- relative to |S| that is c u when G has most of its
+    energy outside the factors' spans (|S| ~ |G| / (lamA lamG)), and grows by the damped
+    condition sigma / lambda when G lies in them (as a layer's own gradient does).
+    Returns the relative Frobenius bound (at least 1e-2)."""
+    G = np.asarray(G, dtype=np.float64)
+    S_ref = np.asarray(S_ref, dtype=np.float64)
+    scale = np.linalg.norm(G) / (lamA * lamG) / max(np.linalg.norm(S_ref), 1e-300)
+    return max(1e-2, c * 2.0 ** -8 * scale)
 
 
 def gapped_prefix(lam, r, thr):
@@ -65,14 +80,18 @@ def gapped_prefix(lam, r, thr):
 
 
 def max_sin_theta(U1t, U2t, k):
-    """sin of the largest principal angle between the spans of the first k rows."""
+    """sin of the largest principal angle between the spans of the first k rows: the
+    2-norm of the part of A = U1[:k] outside span(B = U2[:k]), A - (A B^T) B (B
+    orthonormalised first).  Unlike sqrt(1 - cos^2) it stays accurate for tiny angles
+    and is blind to rows of A that are a little off unit norm."""
     if k <= 0:
         return 0.0
     A = np.asarray(U1t, dtype=np.float64)[:k]
     B = np.asarray(U2t, dtype=np.float64)[:k]
-    s = np.linalg.svd(A @ B.T, compute_uv=False)
-    c = float(np.clip(s.min(), -1.0, 1.0))
-    return float(np.sqrt(max(0.0, 1.0 - c * c)))
+    Qb, _ = np.linalg.qr(B.T)  # d x k orthonormal basis of span(B)
+    Qa, _ = np.linalg.qr(A.T)
+    R = Qa - Qb @ (Qb.T @ Qa)
+    return float(np.linalg.norm(R, 2))
 
 
 def judge_step(Ug, sg, Uo_full, so_full, k, dtype, tol, orth_tol=None):
@@ -95,13 +114,16 @@ def judge_step(Ug, sg, Uo_full, so_full, k, dtype, tol, orth_tol=None):
     sg = np.asarray(sg, dtype=np.float64)[:k]
     Ug = np.asarray(Ug, dtype=np.float64)[:k]
     out = {}
+    bad = []
     es = rel(sg, so[:k])
     out["sigma"] = es
-    assert es < tol, ("sigma", es)
+    if not es < tol:
+        bad.append(("sigma", es))
     s1 = max(so[0], 1e-300) if len(so) else 1.0
     mode = float(np.abs(sg - so[:k]).max() / s1) if k else 0.0
     out["mode"] = mode
-    assert mode < MODE_TOL[dtype], ("per-mode sigma", mode)
+    if not mode < MODE_TOL[dtype]:
+        bad.append(("per-mode sigma", mode))
     worst_angle = 0.0
     gapped = [j for j in range(1, k + 1)
               if so[j - 1] > 0 and (so[j - 1] - (so[j] if j < len(so) else 0.0)) / so[j - 1] > 1e-3]
@@ -112,7 +134,8 @@ def judge_step(Ug, sg, Uo_full, so_full, k, dtype, tol, orth_tol=None):
         bound = min(1.0, 10.0 * MODE_TOL[dtype] * s1 / (so[j - 1] - nxt))
         st = max_sin_theta(Ug, Uo, j)
         worst_angle = max(worst_angle, st / bound)
-        assert st <= bound, ("subspace", j, st, bound)
+        if not st <= bound:
+            bad.append(("subspace", j, st, bound))
     out["angle_frac"] = worst_angle
     tie = truncation_gap(so, k) < NEAR_TIE[dtype] if k < len(so) else False
     out["tie"] = bool(tie)
@@ -122,10 +145,13 @@ def judge_step(Ug, sg, Uo_full, so_full, k, dtype, tol, orth_tol=None):
     else:
         er = lowrank_rel_err(Ug, sg, Uo[:k], so[:k])
     out["recon"] = er
-    assert er < tol, ("reconstruction", er, "near tie" if tie else "")
+    if not er < tol:
+        bad.append(("reconstruction", er, "near tie" if tie else ""))
     if orth_tol is not None:
         pos = sg > 0
         oe = orth_err(Ug[pos])
         out["orth"] = oe
-        assert oe < orth_tol, ("orthonormality", oe)
+        if not oe < orth_tol:
+            bad.append(("orthonormality", oe))
+    assert not bad, (bad, out)
     return out

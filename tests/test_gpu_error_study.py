@@ -62,7 +62,9 @@ def test_mlp_error_study_pinned_to_oracle(oracle):
             assert abs(got[3] - m4) <= 1e-9 + 1e-6 * abs(m4), (l, a, got[3], m4)
             worst = max(worst, abs(got[2] - m3))
     for before, after in res["correction_checks"]:
-        assert after <= before * (1 + 1e-3)
+        # the footnote's claim holds in exact arithmetic; FP32 rounding adds noise at
+        # about u_32 of a column norm once the representation is already this close
+        assert after <= before * (1 + 1e-3) + 1e-6, (before, after)
     h = np.asarray(res["history"]["b-kfac"])
     assert np.all(np.isfinite(h))
     print(f"MLP study: last-step metric 3 vs the oracle's reference, largest difference {worst:.2e}; means",
