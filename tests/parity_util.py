@@ -56,11 +56,11 @@ NEAR_TIE = {0: 1e3 * 2.0 ** -53, 1: 1e3 * 2.0 ** -24, 2: 10 * 2.0 ** -8}
 MODE_TOL = {0: 1e-12, 1: 2e-5, 2: 8e-3}
 
 
-def mixed_apply_bound(G, S_ref, lamA, lamG, c=4.0):
+def mixed_apply_bound(G, S_ref, lamA, lamG, c=2.0):
     """Stated bound of a mixed-precision inverse application: S = G / (lamA lamG) +
     W1 U_A^T + U_G W2 adds terms of size |G| / (lamA lamG) that cancel in the span of the
     factors, each carrying the BF16 rounding (u = 2^-8) of its operands, so the error is
-    about c u |G|_F / (lamA lamG) -- relative to |S| that is c u when G has most of its
+    about c u |G|_F / (lamA lamG), c = 2 -- relative to |S| that is c u when G has most of its
     energy outside the factors' spans (|S| ~ |G| / (lamA lamG)), and grows by the damped
     condition sigma / lambda when G lies in them (as a layer's own gradient does).
     Returns the relative Frobenius bound (at least 1e-2)."""
