@@ -715,7 +715,7 @@ def run_mlp(args, world, rank, local):
             shard.exchange_steps(S_all, parts, rank)
 
     stream = torch.cuda.current_stream()
-    for t in range(args.warmup + 1):
+    for t in range(args.warmup + 1 if not args.mlp_only_mixed else 0):
         plain_step(t)
     torch.cuda.synchronize()
 
@@ -735,14 +735,18 @@ def run_mlp(args, world, rank, local):
         return shard.max_over_ranks(float(sum(a.elapsed_time(b) for a, b in evs)), device=dev) / steps
 
     with ClockSampler(local) as clk:
-        ms_plain = timed(lambda t: plain_step(args.warmup + 1 + t), args.steps, stream)
+        ms_plain = timed(lambda t: plain_step(args.warmup + 1 + t), args.steps if not args.mlp_only_mixed else 0,
+                         stream) if not args.mlp_only_mixed else float("nan")
     st = bkfac.bkfac_status()
     if st != bkfac.OK:
         raise RuntimeError(f"plain MLP step: {bkfac.strerror(st)}")
     results["plain_f32"] = {"ms_per_step": ms_plain, "value": 2 * L * 1000.0 / ms_plain}
 
     # batched paths: one graph per step over this rank's layers, fresh inputs copied in
-    for name, dtype in (("batched_f32_graph", bkfac.F32), ("batched_mixed_bf16_graph", bkfac.MIXED_BF16)):
+    paths = (("batched_f32_graph", bkfac.F32), ("batched_mixed_bf16_graph", bkfac.MIXED_BF16))
+    if args.mlp_only_mixed:
+        paths = paths[1:]
+    for name, dtype in paths:
         layers_b = make_layers(dtype)
         batch = bkfac.Batch(layers_b, MLP_N, dtype, tune_cache=tune_cache)
         XA0, XG0, G0 = pool[0]
@@ -1225,6 +1229,8 @@ def main():
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the small FP64, uneven-batch and MLP workloads of the default run")
     ap.add_argument("--workload", default="wide-layer", choices=["wide-layer", "mlp"])
+    ap.add_argument("--mlp-only-mixed", action="store_true",
+                    help="with --workload mlp: time only the batched mixed path (for launch lists)")
     pc = ap.add_argument_group("profiler case (--profile-case)")
     pc.add_argument("--profile-case", action="store_true", help="run one factor's updates for a kernel profiler")
     pc.add_argument("--d", type=int, default=4097)
