@@ -230,26 +230,61 @@ __global__ void __launch_bounds__(THREADS, 2) tma_gemm_kernel(const __grid_const
     const bool with_d = !split && g.D != nullptr && beta != 0.f;
     if (!s_fail) {
       if (g.c_rowmaj || split) {
+        // rows leave whole: lane l owns columns 4 l .. 4 l + 3 of the tile (16-byte
+        // accesses), and each warp keeps the D rows of eight output rows in flight
         float* out = split ? (float*)g.partial + (int64_t)blockIdx.z * g.M * g.N : (float*)g.C;
         const int64_t ldo = split ? g.N : g.ldc;
-        for (int r = ew; r < BM; r += 4) {
-          const int m = m0 + r;
-          if (m >= g.M) break;
-          const float rsm = (!split && g.rs) ? (float)g.rs[m] : 1.f;
-          for (int c = lane; c < BN; c += 32) {
-            const int n = n0 + c;
-            if (n >= g.N) break;
-            float o = T[r * OLD + c];
-            if (!split) {
-              o *= alpha * rsm;
-              if (g.cs) o *= (float)g.cs[n];
-              if (with_d) {
-                float dv = ((const float*)g.D)[(int64_t)m * g.ldd + n];
-                if (g.ds) dv *= (float)g.ds[n];
-                o += beta * dv;
+        const int n = n0 + 4 * lane;
+        const bool full = n + 4 <= g.N;
+        const bool vec_o = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) && (ldo & 3) == 0;
+        const bool vec_d = with_d && ((reinterpret_cast<uintptr_t>(g.D) & 15u) == 0) && (g.ldd & 3) == 0;
+        float csv[4], dsv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool in = n + j < g.N;
+          csv[j] = (!split && g.cs && in) ? (float)g.cs[n + j] : 1.f;
+          dsv[j] = (g.ds && in) ? (float)g.ds[n + j] : 1.f;
+        }
+        constexpr int RB = 8;
+        for (int r0 = ew; r0 < BM; r0 += 4 * RB) {
+          float4 dq[RB];
+#pragma unroll
+          for (int u = 0; u < RB; ++u) {
+            const int m = m0 + r0 + 4 * u;
+            dq[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (with_d && m < g.M && n < g.N) {
+              const float* drow = (const float*)g.D + (int64_t)m * g.ldd + n;
+              if (full && vec_d) {
+                dq[u] = __ldg(reinterpret_cast<const float4*>(drow));
+              } else {
+                dq[u].x = drow[0];
+                if (n + 1 < g.N) dq[u].y = drow[1];
+                if (n + 2 < g.N) dq[u].z = drow[2];
+                if (n + 3 < g.N) dq[u].w = drow[3];
               }
             }
-            out[(int64_t)m * ldo + n] = o;
+          }
+#pragma unroll
+          for (int u = 0; u < RB; ++u) {
+            const int r = r0 + 4 * u, m = m0 + r;
+            if (m >= g.M || n >= g.N) continue;
+            const float rsm = (!split && g.rs) ? (float)g.rs[m] : 1.f;
+            const float dv[4] = {dq[u].x, dq[u].y, dq[u].z, dq[u].w};
+            float o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              o[j] = T[r * OLD + 4 * lane + j];
+              if (!split) o[j] *= alpha * rsm * csv[j];
+              if (with_d) o[j] += beta * dv[j] * dsv[j];
+            }
+            float* orow = out + (int64_t)m * ldo + n;
+            if (full && vec_o) {
+              *reinterpret_cast<float4*>(orow) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                if (n + j < g.N) orow[j] = o[j];
+            }
           }
         }
       } else {
