@@ -374,9 +374,13 @@ int bkfac_tune(const bkfac_factor* f, int n, const char* cache_path);
 
 /* ---- batched calls: all factors of all FC layers -------------------------
  * A batch groups the two factors of nlayers layers (uneven d, r) with a
- * common batch width n and dtype.  Each phase of the update and of the apply
- * runs as one grouped launch over every factor (or every layer); the whole
- * step can be captured once into a CUDA graph and replayed. */
+ * common batch width n and dtype.  An update runs in three stages: every
+ * factor's work up to its eigensolve, forked onto one worker stream per
+ * factor; the eigensolves, one grouped launch per eigensolve shape (one
+ * thread-block cluster per factor, the launch shape of each group tuned for
+ * its size when a tune cache is given); the rest of every update, forked
+ * again.  The apply forks one stream per layer.  The whole step can be
+ * captured once into a CUDA graph and replayed. */
 typedef struct bkfac_layer_desc {
   bkfac_factor A;  /* forward factor, d = d_in (+1 for the bias) */
   bkfac_factor G;  /* backward factor, d = d_out */
@@ -386,9 +390,14 @@ typedef struct bkfac_batch bkfac_batch;
 
 /* Creates a batch over caller-owned factor buffers (copied descriptors; the
  * batch advances r_cur / step of its copies).  The handle allocates its own
- * device workspace and descriptor tables once, here (cudaMalloc), never on
- * the per-step path.  tune_cache: path of a text file of tuned tile choices
- * (may be NULL; read if present).  Returns NULL on error. */
+ * device workspace and worker streams once, here (cudaMalloc), never on the
+ * per-step path.  tune_cache: path of a text file of tuned eigensolve launch
+ * shapes (may be NULL; read if present).  With a cache the batch times its
+ * eigensolve groups here (temporary device memory, outside any capture) and
+ * writes the choices back; without one it takes each shape's tuned or
+ * default plan, with the block exchange over distributed shared memory while
+ * every group's clusters fit on the GPU at once and through L2 otherwise.
+ * Returns NULL on error. */
 bkfac_batch* bkfac_batch_create(const bkfac_layer_desc* layers, int nlayers, int n, int dtype,
                                 const char* tune_cache);
 
