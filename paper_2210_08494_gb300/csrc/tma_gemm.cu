@@ -20,11 +20,10 @@
 //     per stage) with shared-memory descriptors of the swizzled K-major layout,
 //     and frees each stage by tcgen05.commit to its "empty" mbarrier;
 //   * four warps read the FP32 accumulator back from tensor memory
-//     (tcgen05.ld 32x32b, one TMEM lane quadrant per warp) into a shared tile;
-//     then all six warps apply the epilogue alpha rs[m] cs[n] acc + beta ds[n]
-//     D(m, n) and write C row- or column-major with coalesced 16-byte accesses
-//     (eight rows of D in flight per warp), or split-K partials (row-major
-//     M x N per split) for splitk_reduce_f32.
+//     (tcgen05.ld 32x32b, one TMEM lane quadrant per warp) into a shared tile,
+//     then apply the epilogue alpha rs[m] cs[n] acc + beta ds[n] D(m, n) and
+//     write C row- or column-major with coalesced accesses, or split-K partials
+//     (row-major M x N per split) for splitk_reduce_f32.
 //
 // Every wait is bounded: a stage or accumulator that never completes records
 // BKFAC_ETIMEOUT and the kernel returns.  The TMA coordinates along K are
@@ -223,13 +222,8 @@ __global__ void __launch_bounds__(THREADS, 2) tma_gemm_kernel(const __grid_const
       for (int c0 = 0; c0 < BN; ++c0) T[row * OLD + c0] = 0.f;
       if (!done) s_fail = 1;
     }
-  }
-  // every warp: the staged tile is complete (and the producer and MMA loops are done)
-  asm volatile("barrier.sync 1, %0;" ::"r"(THREADS) : "memory");
-  {
-    constexpr int NW = THREADS / 32;
-    const int ew = warp;  // all six warps write the tile out
-    const float* T = reinterpret_cast<const float*>(sm);
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
+    const int ew = warp - 2;                        // 0..3
     const bool split = g.splits > 1;
     const float alpha = (float)g.alpha;
     const float beta = (float)(g.beta_dev ? *g.beta_dev : g.beta);
@@ -252,13 +246,13 @@ __global__ void __launch_bounds__(THREADS, 2) tma_gemm_kernel(const __grid_const
           dsv[j] = (g.ds && in) ? (float)g.ds[n + j] : 1.f;
         }
         constexpr int RB = 8;
-        for (int r0 = ew; r0 < BM; r0 += NW * RB) {
+        for (int r0 = ew; r0 < BM; r0 += 4 * RB) {
           float4 dq[RB];
 #pragma unroll
           for (int u = 0; u < RB; ++u) {
-            const int m = m0 + r0 + NW * u;
+            const int m = m0 + r0 + 4 * u;
             dq[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (with_d && r0 + NW * u < BM && m < g.M && n < g.N) {
+            if (with_d && m < g.M && n < g.N) {
               const float* drow = (const float*)g.D + (int64_t)m * g.ldd + n;
               if (full && vec_d) {
                 dq[u] = __ldg(reinterpret_cast<const float4*>(drow));
@@ -272,8 +266,8 @@ __global__ void __launch_bounds__(THREADS, 2) tma_gemm_kernel(const __grid_const
           }
 #pragma unroll
           for (int u = 0; u < RB; ++u) {
-            const int r = r0 + NW * u, m = m0 + r;
-            if (r >= BM || m >= g.M || n >= g.N) continue;
+            const int r = r0 + 4 * u, m = m0 + r;
+            if (m >= g.M || n >= g.N) continue;
             const float rsm = (!split && g.rs) ? (float)g.rs[m] : 1.f;
             const float dv[4] = {dq[u].x, dq[u].y, dq[u].z, dq[u].w};
             float o[4];
@@ -297,7 +291,7 @@ __global__ void __launch_bounds__(THREADS, 2) tma_gemm_kernel(const __grid_const
         for (int rb = 0; rb < BM; rb += 32) {
           const int r = rb + lane, m = m0 + r;
           const float rsm = (g.rs && m < g.M) ? (float)g.rs[m] : 1.f;
-          for (int c = ew; c < BN; c += NW) {
+          for (int c = ew; c < BN; c += 4) {
             const int n = n0 + c;
             if (m >= g.M || n >= g.N) continue;
             float o = T[r * OLD + c] * alpha * rsm;
