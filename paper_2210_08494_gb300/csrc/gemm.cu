@@ -288,6 +288,44 @@ __global__ void __launch_bounds__(256) splitk_reduce(const GemmArgs g) {
   }
 }
 
+// The same sum for a column-major C: 32 x 32 tiles through shared memory, so
+// that the row-major partials are read along n and C (and D) are written along m,
+// both contiguous.  Same summation order as splitk_reduce.
+template <typename Acc, typename TOut>
+__global__ void __launch_bounds__(256) splitk_reduce_cm(const GemmArgs g) {
+  __shared__ Acc t[32][33];
+  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int64_t total = (int64_t)g.M * g.N;
+  const Acc* P = (const Acc*)g.partial;
+  for (int i = ty; i < 32; i += 8) {
+    const int m = m0 + i, n = n0 + tx;
+    Acc sum = Acc(0);
+    if (m < g.M && n < g.N) {
+      const int64_t src = (g.sym && (m / BM) > (n / BN)) ? (int64_t)n * g.N + m : (int64_t)m * g.N + n;
+      for (int z = 0; z < g.splits; ++z) sum += P[(int64_t)z * total + src];
+    }
+    t[i][tx] = sum;
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int n = n0 + i, m = m0 + tx;
+    if (m < g.M && n < g.N) epilogue_store<Acc, TOut>(g, m, n, t[tx][i]);
+  }
+}
+
+template <typename Acc, typename TOut>
+void launch_splitk_reduce(const GemmArgs& a, cudaStream_t s) {
+  if (a.c_rowmaj) {
+    const int64_t total = (int64_t)a.M * a.N;
+    const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
+    splitk_reduce<Acc, TOut><<<blocks, 256, 0, s>>>(a);
+  } else {
+    dim3 grid((unsigned)ceil_div(a.N, 32), (unsigned)ceil_div(a.M, 32));
+    splitk_reduce_cm<Acc, TOut><<<grid, 256, 0, s>>>(a);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // FP32 SIMT GEMM for the large products: 128 x 128 tiles, 8 x 8 outputs per
 // thread (four 4 x 4 quadrants at offsets 0 / 64 so shared-memory reads are
@@ -564,9 +602,7 @@ int run_large_f32(const GemmArgs& g, cudaStream_t s) {
     sgemm_large_kernel<false, false><<<grid, LNT, 0, s>>>(a);
   note_launches(1);
   if (a.splits > 1) {
-    int64_t total = (int64_t)a.M * a.N;
-    int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
-    splitk_reduce<float, float><<<blocks, 256, 0, s>>>(a);
+    launch_splitk_reduce<float, float>(a, s);
     note_launches(1);
   }
   return (int)cudaGetLastError();
@@ -596,9 +632,7 @@ int run_typed(const GemmArgs& g, cudaStream_t s) {
     gemm_kernel<TIn, Acc, TOut, false, false><<<grid, NT, 0, s>>>(a);
   note_launches(1);
   if (a.splits > 1) {
-    int64_t total = (int64_t)a.M * a.N;
-    int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
-    splitk_reduce<Acc, TOut><<<blocks, 256, 0, s>>>(a);
+    launch_splitk_reduce<Acc, TOut>(a, s);
     note_launches(1);
   }
   return (int)cudaGetLastError();
@@ -626,17 +660,13 @@ int gram_run_comp(const GemmArgs& g, cudaStream_t s) {
   a.splits = (int)std::max<int64_t>(1, ceil_div(std::max(K, 1), a.k_chunk));
   dim3 grid((unsigned)ceil_div(a.N, BN), (unsigned)ceil_div(a.M, BM), (unsigned)a.splits);
   gram_comp_kernel<<<grid, NT, 0, s>>>(a);
-  const int64_t total = (int64_t)a.M * a.N;
-  const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
-  splitk_reduce<double, double><<<blocks, 256, 0, s>>>(a);
+  launch_splitk_reduce<double, double>(a, s);
   note_launches(2);
   return (int)cudaGetLastError();
 }
 
 int splitk_reduce_f32(const GemmArgs& g, cudaStream_t s) {
-  const int64_t total = (int64_t)g.M * g.N;
-  const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
-  splitk_reduce<float, float><<<blocks, 256, 0, s>>>(g);
+  launch_splitk_reduce<float, float>(g, s);
   note_launches(1);
   return (int)cudaGetLastError();
 }
@@ -654,7 +684,7 @@ int gemm_run(const GemmArgs& g, DType in_t, DType acc_t, DType out_t, cudaStream
       const int64_t tiles = ceil_div(g.M, LBM) * ceil_div(g.N, LBN);
       const int64_t room = a.partial ? (int64_t)(a.partial_bytes / ((size_t)g.M * g.N * sizeof(float))) : 0;
       if (a.splits <= 1 && tiles < sm_count() && room >= 2)
-        a.splits = (int)std::min<int64_t>(std::min<int64_t>(4, 304 / tiles), room);
+        a.splits = (int)std::min<int64_t>(std::min<int64_t>(4, 2 * sm_count() / tiles), room);
       if (a.splits > 1 && room < a.splits) a.splits = (int)std::max<int64_t>(1, room);
       return run_large_f32(a, s);
     }
