@@ -359,6 +359,18 @@ def timed_steps(torch, stream, fn, steps, flush):
     return float(sum(a.elapsed_time(b) for a, b in evs)) / steps
 
 
+def tune_products(bkfac, torch, fn, cache):
+    """Run fn() once (untimed) with the library noting the FP32 product shapes it
+    launches, then time the candidates of each new shape and keep the fastest."""
+    torch.cuda.synchronize()
+    bkfac.bkfac_gemm_tune_begin()
+    try:
+        fn()
+    finally:
+        torch.cuda.synchronize()
+        bkfac.bkfac_gemm_tune_end(cache)
+
+
 def run_workload_batch(args, bkfac, torch, dev, flush, peaks, sources, shapes, n, inputs, grads, name,
                        plain=True, variants=(("batched_f32_graph", "f32", 0),
                                              ("batched_mixed_bf16_graph", "mixed", 0))):
@@ -406,7 +418,10 @@ def run_workload_batch(args, bkfac, torch, dev, flush, peaks, sources, shapes, n
                 bkfac.bkfac_apply(a, g, LAM, LAM, grads[l], S[l])
 
         with torch.cuda.stream(stream):
-            for t in range(args.warmup + 1):
+            plain_step(0)
+            # the products' tile shapes and K splits, tuned on the step's own shapes
+            tune_products(bkfac, torch, lambda: plain_step(1), tune_cache)
+            for t in range(2, args.warmup + 1):
                 plain_step(t)
         stream.synchronize()
         bkfac.bkfac_trace_enable(True)
@@ -441,9 +456,15 @@ def run_workload_batch(args, bkfac, torch, dev, flush, peaks, sources, shapes, n
                 dst.copy_(src)
 
         with torch.cuda.stream(stream):
-            for t in range(2):
-                load(t)
+            load(0)
+            batch.update(xa, xg, RHO)
+            load(1)
+
+            def eager_step():
                 batch.update(xa, xg, RHO)
+                batch.apply(grads, Sb, [LAM] * L, [LAM] * L)
+
+            tune_products(bkfac, torch, eager_step, tune_cache)
             load(2)
             batch.step_graph(xa, xg, RHO, grads, Sb, [LAM] * L, [LAM] * L, capture=True)
             for t in range(args.warmup):
@@ -715,8 +736,12 @@ def run_mlp(args, world, rank, local):
             shard.exchange_steps(S_all, parts, rank)
 
     stream = torch.cuda.current_stream()
-    for t in range(args.warmup + 1 if not args.mlp_only_mixed else 0):
-        plain_step(t)
+    if not args.mlp_only_mixed:
+        plain_step(0)
+        # the products' tile shapes and K splits, tuned on the step's own shapes (untimed)
+        tune_products(bkfac, torch, lambda: plain_step(1), tune_cache)
+        for t in range(2, args.warmup + 1):
+            plain_step(t)
     torch.cuda.synchronize()
 
     def timed(fn, steps, s, clk_holder=None):
@@ -762,9 +787,15 @@ def run_mlp(args, world, rank, local):
 
         s2 = torch.cuda.Stream(device=dev)
         with torch.cuda.stream(s2):
-            for t in range(2):
-                load(t)
+            load(0)
+            batch.update(xa, xg, RHO)
+            load(1)
+
+            def eager_step():
                 batch.update(xa, xg, RHO)
+                batch.apply(gb, Sb, lam, lam)
+
+            tune_products(bkfac, torch, eager_step, tune_cache)
             load(2)
             batch.step_graph(xa, xg, RHO, gb, Sb, lam, lam, capture=True)
             for t in range(args.warmup):
@@ -860,7 +891,9 @@ def run_gpu(args, world, rank, local):
         if world > 1:
             shard.exchange_steps(S_all, parts, rank)  # every rank receives every layer's step
 
-    for t in range(args.warmup):
+    # the products' tile shapes and K splits, tuned on the step's own shapes (untimed)
+    tune_products(bkfac, torch, lambda: step(0), tune_cache)
+    for t in range(1, args.warmup):
         step(t)
     torch.cuda.synchronize()
     st = bkfac.bkfac_status()

@@ -372,6 +372,29 @@ const char* bkfac_trace_phase_name(int id);
  * only changes launch shapes, never the decomposition computed. */
 int bkfac_tune(const bkfac_factor* f, int n, const char* cache_path);
 
+/* GEMM autotuning for the FP32 products (CUDA-core GEMMs: the projections,
+ * residuals, CholeskyQR solves, rotations and apply passes of the FP32 and FP64-
+ * accumulated paths, and the small products of every apply).
+ *   bkfac_gemm_tune_begin()  from now on the library notes the shape of every
+ *       FP32 product it launches (M, N, the K segments, the operand and output
+ *       layouts, a D term, and the partial-sum buffer the call has); the calls
+ *       themselves run as before.
+ *   bkfac_gemm_tune_end(cache_path)  stops noting; reads cache_path if present
+ *       (may be NULL); for every noted shape not yet in the process-wide table,
+ *       times the candidates -- 64 x 64 or 128 x 128 output tiles, K split into
+ *       1 .. 32 pieces within the partial buffer the call had -- on synthetic
+ *       operands of that shape, and records the fastest; writes the table
+ *       (with the eigensolve choices) to cache_path.  Later calls whose shape
+ *       is in the table use its choice when their layout and partial buffer
+ *       allow it, else the built-in heuristic.  Allocates temporary device
+ *       memory and synchronises: call it outside any stream capture.  A choice
+ *       changes the order in which K terms are summed (FP32 rounding), not the
+ *       product computed.
+ * Both return BKFAC_OK or an error code (BKFAC_ECUDA when a device call failed;
+ * the table then keeps the shapes that were tuned). */
+int bkfac_gemm_tune_begin(void);
+int bkfac_gemm_tune_end(const char* cache_path);
+
 /* ---- batched calls: all factors of all FC layers -------------------------
  * A batch groups the two factors of nlayers layers (uneven d, r) with a
  * common batch width n and dtype.  An update runs in three stages: every

@@ -105,6 +105,8 @@ def load(build_if_missing: bool = True):
             "bkfac_batch_reorth": ([P, P], I),
             "bkfac_trace_enable": ([I], I),
             "bkfac_tune": ([FP, I, ctypes.c_char_p], I),
+            "bkfac_gemm_tune_begin": ([], I),
+            "bkfac_gemm_tune_end": ([ctypes.c_char_p], I),
             "bkfac_trace_read": ([ctypes.POINTER(D), ctypes.POINTER(I64), I, ctypes.POINTER(I64)], I),
             "bkfac_trace_phase_name": ([I], ctypes.c_char_p),
             "bkfac_set_sweep_cap": ([I], I),
@@ -131,7 +133,8 @@ def exported_symbols():
               "bkfac_trace_read", "bkfac_trace_phase_name", "bkfac_apply_noalloc", "bkfac_tune", "bkfac_batch_reorth",
               "bkfac_apply_factored_workspace_size", "bkfac_apply_factored", "bkfac_ea_update",
               "bkfac_correct_workspace_size", "bkfac_correct", "bkfac_rsvd_workspace_size", "bkfac_rsvd",
-              "bkfac_set_sweep_cap", "bkfac_selftest_wait_timeout"):
+              "bkfac_set_sweep_cap", "bkfac_selftest_wait_timeout", "bkfac_gemm_tune_begin",
+              "bkfac_gemm_tune_end"):
         if hasattr(lib, n):
             names.append(n)
     return names
@@ -486,3 +489,13 @@ class Batch:
 def bkfac_tune(f: Factor, n: int, cache_path: str | None = None):
     """Autotune the eigensolve launch shape of f at batch width n (see include/bkfac.h)."""
     _check(load().bkfac_tune(ctypes.byref(f.desc), int(n), cache_path.encode() if cache_path else None), "bkfac_tune")
+
+
+def bkfac_gemm_tune_begin():
+    """Start noting the FP32 product shapes the library launches (see include/bkfac.h)."""
+    _check(load().bkfac_gemm_tune_begin(), "bkfac_gemm_tune_begin")
+
+
+def bkfac_gemm_tune_end(cache_path: str | None = None):
+    """Stop noting; time the candidates of every noted shape and keep the fastest."""
+    _check(load().bkfac_gemm_tune_end(cache_path.encode() if cache_path else None), "bkfac_gemm_tune_end")

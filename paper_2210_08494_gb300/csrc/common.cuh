@@ -258,6 +258,24 @@ bool tune_lookup(int rows, int cols, DType jt, int* b, int* dsm);
 int tune_shape(int rows, int cols, DType jt);
 int tune_load(const char* path);
 int tune_save(const char* path);
+// FP32 SIMT products (gemm.cu / tune.cu): a choice of kernel (GEMM_SMALL: 64 x 64
+// tiles, GEMM_LARGE: 128 x 128 tiles) and K splits per product shape.  While
+// recording is on, gemm_run notes every shape it dispatches (with the partial
+// buffer room of the call); gemm_tune_recorded times the candidates of each noted
+// shape not yet in the table on synthetic operands and keeps the fastest.
+enum { GEMM_SMALL = 1, GEMM_LARGE = 2 };
+struct GemmPick {
+  int kernel;
+  int splits;
+};
+void gemm_record(bool on);
+void gemm_note_shape(const GemmArgs& g, int64_t room);
+bool gemm_pick_lookup(const GemmArgs& g, GemmPick* out);
+int gemm_tune_recorded();
+// launch an FP32 product with a given choice (checked: BKFAC_EINVAL when the
+// layout or the partial buffer does not allow it)
+int gemm_run_choice(const GemmArgs& g, GemmPick pick, cudaStream_t s);
+bool gemm_choice_ok(const GemmArgs& g, GemmPick pick);
 // shared memory bytes one CTA needs for a problem
 size_t jacobi_smem_bytes(int b, int rows_pad, DType j_t);
 // A caller's choice of the eigensolve's launch shape: the block-width cap (0: the

@@ -314,9 +314,12 @@ __global__ void __launch_bounds__(256) splitk_reduce_cm(const GemmArgs g) {
   }
 }
 
+// The transposing kernel pays off for tall column-major outputs (the residual, the
+// CholeskyQR solve, the rotation, the apply's T1 / T2: a million elements and more);
+// small outputs (U^T X, the Gram matrices) keep more blocks in flight with the flat one.
 template <typename Acc, typename TOut>
 void launch_splitk_reduce(const GemmArgs& a, cudaStream_t s) {
-  if (a.c_rowmaj) {
+  if (a.c_rowmaj || a.sym || (int64_t)a.M * a.N < (int64_t)256 * 1024) {
     const int64_t total = (int64_t)a.M * a.N;
     const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
     splitk_reduce<Acc, TOut><<<blocks, 256, 0, s>>>(a);
@@ -671,6 +674,24 @@ int splitk_reduce_f32(const GemmArgs& g, cudaStream_t s) {
   return (int)cudaGetLastError();
 }
 
+int64_t partial_room(const GemmArgs& g) {
+  return g.partial ? (int64_t)(g.partial_bytes / ((size_t)std::max(g.M, 1) * std::max(g.N, 1) * sizeof(float))) : 0;
+}
+
+bool gemm_choice_ok(const GemmArgs& g, GemmPick pick) {
+  if (g.sym || g.round_bf16 || g.tf32x3) return false;
+  if (pick.splits < 1 || (pick.splits > 1 && pick.splits > partial_room(g))) return false;
+  if (pick.kernel == GEMM_LARGE) return large_layout_ok(g);
+  return pick.kernel == GEMM_SMALL;
+}
+
+int gemm_run_choice(const GemmArgs& g, GemmPick pick, cudaStream_t s) {
+  if (!gemm_choice_ok(g, pick)) return BKFAC_EINVAL;
+  GemmArgs a = g;
+  a.splits = pick.splits;
+  return pick.kernel == GEMM_LARGE ? run_large_f32(a, s) : run_typed<float, float, float>(a, s);
+}
+
 int gemm_run(const GemmArgs& g, DType in_t, DType acc_t, DType out_t, cudaStream_t s) {
   if (in_t == DT_F64 && acc_t == DT_F64 && out_t == DT_F64) return run_typed<double, double, double>(g, s);
   // mixed precision (BF16 operands, FP32 accumulation): the tensor cores
@@ -678,6 +699,11 @@ int gemm_run(const GemmArgs& g, DType in_t, DType acc_t, DType out_t, cudaStream
       tc_gemm_enabled())
     return tc_gemm_run(g, s);
   if (in_t == DT_F32 && acc_t == DT_F32 && out_t == DT_F32) {
+    if (g.M <= 0 || g.N <= 0) return (int)cudaSuccess;
+    gemm_note_shape(g, partial_room(g));
+    // a tuned choice for this shape, when it fits this call
+    GemmPick pick;
+    if (!g.sym && gemm_pick_lookup(g, &pick) && gemm_choice_ok(g, pick)) return gemm_run_choice(g, pick, s);
     if (large_ok(g)) {
       // enough CTAs for the GPU: split K when the output has few 128 x 128 tiles
       GemmArgs a = g;

@@ -10,10 +10,21 @@
 // let more problems run at once, at a cost per problem.  Results live in
 // process-wide tables keyed by (rows, cols, precision[, count]) and can be
 // saved to / loaded from a text file ("rows cols prec b dsm ms" per line for a
-// single problem, "G rows cols prec count b dsm ms" for a group).  The tables
-// only change launch shapes; every candidate computes the same decomposition.
+// single problem, "G rows cols prec count b dsm ms" for a group).  The Jacobi
+// tables only change launch shapes; every candidate computes the same
+// decomposition.
+//
+// A third table holds the FP32 SIMT products: per shape (M, N, K0, K1, operand
+// and output layouts, D term), the kernel (64 x 64 or 128 x 128 tiles) and the
+// number of K splits, timed on synthetic operands of the shapes a workload
+// actually launched (recorded between bkfac_gemm_tune_begin and _end).  A choice
+// changes only the order in which the K terms are summed ("M M N K0 K1 bits
+// kernel splits ms" per line).
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <random>
@@ -34,7 +45,48 @@ std::mutex g_tmu;
 std::map<std::tuple<int, int, int>, TuneEntry> g_table;
 std::map<std::tuple<int, int, int, int>, TuneEntry> g_group_table;
 
+// FP32 products: (M, N, K0, K1, layout bits) -> choice
+using GemmKey = std::tuple<int, int, int, int, int>;
+struct GemmEntry {
+  int kernel;
+  int splits;
+  float ms;
+};
+std::map<GemmKey, GemmEntry> g_gemm_table;
+std::map<GemmKey, int64_t> g_gemm_recorded;  // noted shapes and the least partial room seen
+std::atomic<bool> g_gemm_recording{false};
+
+constexpr int kKmajA = 1, kKmajB = 2, kRowC = 4, kHasD = 8;
+GemmKey gemm_key(const GemmArgs& g) {
+  const int bits = (g.a_kmaj ? kKmajA : 0) | (g.b_kmaj ? kKmajB : 0) | (g.c_rowmaj ? kRowC : 0) |
+                   (g.D != nullptr ? kHasD : 0);
+  return std::make_tuple(g.M, g.N, g.K0, g.K1, bits);
+}
+
 }  // namespace
+
+void gemm_record(bool on) { g_gemm_recording.store(on); }
+
+void gemm_note_shape(const GemmArgs& g, int64_t room) {
+  if (!g_gemm_recording.load(std::memory_order_relaxed) || g.sym) return;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  const GemmKey k = gemm_key(g);
+  auto it = g_gemm_recorded.find(k);
+  if (it == g_gemm_recorded.end())
+    g_gemm_recorded[k] = room;
+  else
+    it->second = std::min(it->second, room);
+}
+
+bool gemm_pick_lookup(const GemmArgs& g, GemmPick* out) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  if (g_gemm_table.empty()) return false;
+  auto it = g_gemm_table.find(gemm_key(g));
+  if (it == g_gemm_table.end()) return false;
+  out->kernel = it->second.kernel;
+  out->splits = it->second.splits;
+  return true;
+}
 
 bool tune_group_lookup(int rows, int cols, DType jt, int count, JacobiChoice* out) {
   std::lock_guard<std::mutex> lk(g_tmu);
@@ -69,7 +121,16 @@ int load_file(const char* path) {
   float ms;
   char line[256];
   while (std::fgets(line, sizeof line, f)) {
-    if (line[0] == 'G') {
+    if (line[0] == 'M') {
+      int M, N, K0, K1, bits, kern, sp;
+      if (std::sscanf(line + 1, "%d %d %d %d %d %d %d %f", &M, &N, &K0, &K1, &bits, &kern, &sp, &ms) == 8 &&
+          M > 0 && N > 0 && K0 >= 0 && K1 >= 0 && (kern == GEMM_SMALL || kern == GEMM_LARGE) && sp >= 1 &&
+          sp <= 64) {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        g_gemm_table[std::make_tuple(M, N, K0, K1, bits)] = GemmEntry{kern, sp, ms};
+        ++n;
+      }
+    } else if (line[0] == 'G') {
       if (std::sscanf(line + 1, "%d %d %d %d %d %d %f", &rows, &cols, &prec, &count, &b, &dsm, &ms) == 7 &&
           b >= 2 && b <= 32 && (b % 2) == 0 && (prec == 0 || prec == 1) && count >= 1) {
         std::lock_guard<std::mutex> lk(g_tmu);
@@ -98,6 +159,10 @@ int save_file(const char* path) {
   for (const auto& kv : g_group_table)
     std::fprintf(f, "G %d %d %d %d %d %d %.4f\n", std::get<0>(kv.first), std::get<1>(kv.first),
                  std::get<2>(kv.first), std::get<3>(kv.first), kv.second.b, kv.second.dsm, kv.second.ms);
+  for (const auto& kv : g_gemm_table)
+    std::fprintf(f, "M %d %d %d %d %d %d %d %.4f\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                 std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first), kv.second.kernel,
+                 kv.second.splits, kv.second.ms);
   std::fclose(f);
   return BKFAC_OK;
 }
@@ -243,6 +308,126 @@ int tune_group(int rows, int cols, DType jt, int count, JacobiChoice* out) {
   return BKFAC_OK;
 }
 
+namespace {
+
+// time one choice of an FP32 product on the synthetic operands in `g`: the fastest
+// of three runs after one warm-up, ms (-1 on failure)
+float time_gemm(const GemmArgs& g, GemmPick pick, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  if (!gemm_choice_ok(g, pick)) return -1.f;
+  float best = -1.f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0, s);
+    const int rc = gemm_run_choice(g, pick, s);
+    cudaEventRecord(e1, s);
+    if (rc != 0 || cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (rep > 0 && (best < 0.f || t < best)) best = t;
+  }
+  return best;
+}
+
+// synthetic operands of one product shape (zeros: the FP32 units' speed does not
+// depend on the values), the candidates timed, the fastest recorded
+int tune_gemm_shape(const GemmKey& key, int64_t room_cap, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  const int M = std::get<0>(key), N = std::get<1>(key), K0 = std::get<2>(key), K1 = std::get<3>(key);
+  const int bits = std::get<4>(key);
+  const int K = K0 + K1;
+  GemmArgs g;
+  std::memset(&g, 0, sizeof g);
+  g.M = M;
+  g.N = N;
+  g.K0 = K0;
+  g.K1 = K1;
+  g.a_kmaj = (bits & kKmajA) != 0;
+  g.b_kmaj = (bits & kKmajB) != 0;
+  g.c_rowmaj = (bits & kRowC) != 0;
+  g.alpha = 1.0;
+  g.beta = (bits & kHasD) ? 1.0 : 0.0;
+  g.splits = 1;
+  auto pad = [](int64_t x) { return round_up(std::max<int64_t>(x, 1), 4); };
+  // element counts: A segments (a_kmaj: M rows of K; else K rows of M), B alike with N, C / D
+  const int64_t lda0 = g.a_kmaj ? pad(K0) : pad(M), lda1 = g.a_kmaj ? pad(K1) : pad(M);
+  const int64_t ldb0 = g.b_kmaj ? pad(K0) : pad(N), ldb1 = g.b_kmaj ? pad(K1) : pad(N);
+  const int64_t na0 = (g.a_kmaj ? M : std::max(K0, 1)) * lda0, na1 = (g.a_kmaj ? M : std::max(K1, 1)) * lda1;
+  const int64_t nb0 = (g.b_kmaj ? N : std::max(K0, 1)) * ldb0, nb1 = (g.b_kmaj ? N : std::max(K1, 1)) * ldb1;
+  const int64_t ldc = g.c_rowmaj ? pad(N) : pad(M), nc = (g.c_rowmaj ? M : N) * ldc;
+  const int64_t mn = (int64_t)M * N;
+  const int64_t room = std::min<int64_t>({room_cap, 32, (int64_t)(256ll << 20) / (mn * 4)});
+  const int64_t counts[7] = {na0, K1 > 0 ? na1 : 0, nb0, K1 > 0 ? nb1 : 0, nc, (bits & kHasD) ? nc : 0,
+                             room >= 2 ? room * mn : 0};
+  size_t off[7], total = 0;
+  for (int i = 0; i < 7; ++i) {
+    off[i] = total;
+    total += (size_t)round_up(counts[i] * 4, 256);
+  }
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, std::max<size_t>(total, 256)) != cudaSuccess) {
+    cudaGetLastError();
+    return BKFAC_ECUDA;
+  }
+  cudaMemsetAsync(buf, 0, total, s);
+  char* b = (char*)buf;
+  g.A0 = b + off[0];
+  g.lda0 = lda0;
+  g.A1 = K1 > 0 ? b + off[1] : nullptr;
+  g.lda1 = lda1;
+  g.B0 = b + off[2];
+  g.ldb0 = ldb0;
+  g.B1 = K1 > 0 ? b + off[3] : nullptr;
+  g.ldb1 = ldb1;
+  g.C = b + off[4];
+  g.ldc = ldc;
+  g.D = (bits & kHasD) ? b + off[5] : nullptr;
+  g.ldd = ldc;
+  g.partial = room >= 2 ? b + off[6] : nullptr;
+  g.partial_bytes = room >= 2 ? (size_t)(room * mn * 4) : 0;
+  GemmEntry best{0, 1, -1.f};
+  for (int kern : {GEMM_SMALL, GEMM_LARGE}) {
+    for (int sp : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
+      if (sp > 1 && (sp > room || K / sp < 64)) continue;
+      const float t = time_gemm(g, GemmPick{kern, sp}, s, e0, e1);
+      if (t > 0.f && (best.ms < 0.f || t < best.ms)) best = GemmEntry{kern, sp, t};
+    }
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(buf);
+  cudaGetLastError();  // a failed candidate must not poison later calls
+  if (best.ms < 0.f) return BKFAC_ECUDA;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  g_gemm_table[key] = best;
+  return BKFAC_OK;
+}
+
+}  // namespace
+
+int gemm_tune_recorded() {
+  std::vector<std::pair<GemmKey, int64_t>> todo;
+  {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    for (const auto& kv : g_gemm_recorded)
+      if (g_gemm_table.find(kv.first) == g_gemm_table.end()) todo.push_back(kv);
+    g_gemm_recorded.clear();
+  }
+  if (todo.empty()) return BKFAC_OK;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return BKFAC_ECUDA;
+  }
+  int rc = BKFAC_OK;
+  for (const auto& kv : todo) {
+    const int r = tune_gemm_shape(kv.first, kv.second, s, e0, e1);
+    if (r != BKFAC_OK) rc = r;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  return rc;
+}
+
 int tune_load(const char* path) { return load_file(path); }
 int tune_save(const char* path) { return save_file(path); }
 
@@ -260,4 +445,17 @@ extern "C" int bkfac_tune(const bkfac_factor* f, int n, const char* cache_path) 
   const int rc = tune_shape(rows, cols, jt);
   if (rc != BKFAC_OK) return rc;
   return tune_save(cache_path);
+}
+
+extern "C" int bkfac_gemm_tune_begin(void) {
+  gemm_record(true);
+  return BKFAC_OK;
+}
+
+extern "C" int bkfac_gemm_tune_end(const char* cache_path) {
+  gemm_record(false);
+  tune_load(cache_path);
+  const int rc = gemm_tune_recorded();
+  const int rs = tune_save(cache_path);
+  return rc != BKFAC_OK ? rc : rs;
 }
