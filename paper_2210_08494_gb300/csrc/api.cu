@@ -1293,6 +1293,10 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.ldd = cap.ld1;
     g.beta = 1.0;
     g.ds = cAo;
+    // pass 1's partial sums are reduced by now: their scratch lets this d_out x kA
+    // product split its short K over more CTAs
+    g.partial = at<void>(ws, cap.o_part1);
+    g.partial_bytes = cap.part1_bytes;
     PHASE(PH_APPLY_SMALL, gemm_run(g, pr.t, pr.acc, pr.t, s));
   }
   // pass 2: S = alpha G + W1 U_A^T + U_G W2

@@ -288,29 +288,56 @@ __global__ void __launch_bounds__(256) splitk_reduce(const GemmArgs g) {
   }
 }
 
-// The same sum for a column-major C: 32 x 32 tiles through shared memory, so
-// that the row-major partials are read along n and C (and D) are written along m,
-// both contiguous.  Same summation order as splitk_reduce.
+// The same sum for a column-major C: 32 x 128 tiles through shared memory.  Each
+// warp reads partial rows along n (four consecutive values per lane, 16-byte
+// loads for FP32 when the row allows it) for every split, and C (and D) are
+// written along m, both contiguous.  Same summation order as splitk_reduce.
+template <typename Acc>
+__device__ __forceinline__ void load4(const Acc* p, int n, int N, bool vec, Acc (&v)[4]) {
+  if constexpr (sizeof(Acc) == 4) {
+    if (vec && n + 4 <= N) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+      v[0] = q.x;
+      v[1] = q.y;
+      v[2] = q.z;
+      v[3] = q.w;
+      return;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = n + j < N ? p[j] : Acc(0);
+}
+
 template <typename Acc, typename TOut>
 __global__ void __launch_bounds__(256) splitk_reduce_cm(const GemmArgs g) {
-  __shared__ Acc t[32][33];
-  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  __shared__ Acc t[32][129];  // [m - m0][n - n0]
+  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 128;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // 8 warps
   const int64_t total = (int64_t)g.M * g.N;
   const Acc* P = (const Acc*)g.partial;
-  for (int i = ty; i < 32; i += 8) {
-    const int m = m0 + i, n = n0 + tx;
-    Acc sum = Acc(0);
+  const bool vec = ((reinterpret_cast<uintptr_t>(P) & 15u) == 0) && (g.N & 3) == 0;
+  const int n = n0 + 4 * lane;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = w + 8 * i, m = m0 + r;
+    Acc sum[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
     if (m < g.M && n < g.N) {
-      const int64_t src = (g.sym && (m / BM) > (n / BN)) ? (int64_t)n * g.N + m : (int64_t)m * g.N + n;
-      for (int z = 0; z < g.splits; ++z) sum += P[(int64_t)z * total + src];
+      const Acc* row = P + (int64_t)m * g.N + n;
+      for (int z = 0; z < g.splits; ++z) {
+        Acc v[4];
+        load4<Acc>(row + (int64_t)z * total, n, g.N, vec, v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sum[j] += v[j];
+      }
     }
-    t[i][tx] = sum;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[r][4 * lane + j] = sum[j];
   }
   __syncthreads();
-  for (int i = ty; i < 32; i += 8) {
-    const int n = n0 + i, m = m0 + tx;
-    if (m < g.M && n < g.N) epilogue_store<Acc, TOut>(g, m, n, t[tx][i]);
+  const int m = m0 + lane;
+  for (int c = w; c < 128; c += 8) {
+    const int nn = n0 + c;
+    if (m < g.M && nn < g.N) epilogue_store<Acc, TOut>(g, m, nn, t[lane][c]);
   }
 }
 
@@ -324,7 +351,7 @@ void launch_splitk_reduce(const GemmArgs& a, cudaStream_t s) {
     const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
     splitk_reduce<Acc, TOut><<<blocks, 256, 0, s>>>(a);
   } else {
-    dim3 grid((unsigned)ceil_div(a.N, 32), (unsigned)ceil_div(a.M, 32));
+    dim3 grid((unsigned)ceil_div(a.N, 128), (unsigned)ceil_div(a.M, 32));
     splitk_reduce_cm<Acc, TOut><<<grid, 256, 0, s>>>(a);
   }
 }
