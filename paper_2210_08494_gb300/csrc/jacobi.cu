@@ -329,6 +329,78 @@ __device__ __forceinline__ unsigned y_mask(unsigned rot) {
   return m;
 }
 
+// FP32, four columns of each block per warp: a meeting's 16 cross pairs as eight
+// half-steps of two pairs on the XOR schedule (step s pairs x_i with y_(i xor s)).
+// In steps 0-1 the half-steps of {x0, x1, y0, y1} and of {x2, x3, y2, y3} touch
+// disjoint columns, and so do those of {x0, x1, y2, y3} and {x2, x3, y0, y1} in
+// steps 2-3: two independent dependency chains, which the scheduler interleaves
+// (one half's rotation FMAs issue while the other waits on its reduction and
+// angle).  Rotations are predicated instead of branched: a pair that does not
+// rotate gets s = tau = 0, which leaves both columns exactly unchanged.
+template <int NV>
+__device__ __forceinline__ unsigned half_step(Col<float, NV>& xa, Col<float, NV>& yb, Col<float, NV>& xc,
+                                              Col<float, NV>& yd, float& a0, float& b0, float& a1, float& b1,
+                                              bool act0, bool act1, float tol2, float tiny, int lane) {
+  constexpr unsigned F = 0xffffffffu;
+  float pd[2] = {dot_lane(xa, yb), dot_lane(xc, yd)};
+  const float g = warp_sum_spread<float, 2>(pd, lane);  // lanes 0-15: pair 0, 16-31: pair 1
+  const bool hi = (lane & 16) != 0;
+  const float am = hi ? a1 : a0, bm = hi ? b1 : b0;
+  const bool on = (hi ? act1 : act0) && am > tiny && bm > tiny && g * g > tol2 * am * bm;
+  float sn = 0.f, tau = 0.f, tg = 0.f;
+  rotation_params(am, bm, g, sn, tau, tg);
+  sn = on ? sn : 0.f;
+  tau = on ? tau : 0.f;
+  tg = on ? tg : 0.f;
+  const float s0 = __shfl_sync(F, sn, 0), t0 = __shfl_sync(F, tau, 0), g0 = __shfl_sync(F, tg, 0);
+  const float s1 = __shfl_sync(F, sn, 16), t1 = __shfl_sync(F, tau, 16), g1 = __shfl_sync(F, tg, 16);
+  const unsigned bal = __ballot_sync(F, on);
+  rotate_lane(xa, yb, s0, t0);
+  rotate_lane(xc, yd, s1, t1);
+  a0 -= g0;
+  b0 += g0;
+  a1 -= g1;
+  b1 += g1;
+  return (bal & 1u) | ((bal >> 15) & 2u);  // bit 0: pair 0 rotated, bit 1: pair 1
+}
+
+// The meeting of x[0..3] with y[0..3]: xf / yf fresh bits (updated as columns
+// rotate), xd / yd the columns rotated here, nrot the rotation count.
+template <int NV>
+__device__ __forceinline__ void meet4_xor(Col<float, NV> (&x)[4], Col<float, NV> (&y)[4], float (&a)[4],
+                                          float (&bn)[4], unsigned& xf, unsigned& yf, float tol2, float tiny,
+                                          int lane, unsigned& xd, unsigned& yd, int& nrot) {
+  auto act = [&](int i, int j) { return (((xf >> i) | (yf >> j)) & 1u) != 0; };
+  auto note = [&](unsigned r, int i0, int j0, int i1, int j1) {
+    const unsigned xm = ((r & 1u) << i0) | (((r >> 1) & 1u) << i1);
+    const unsigned ym = ((r & 1u) << j0) | (((r >> 1) & 1u) << j1);
+    xf |= xm;
+    xd |= xm;
+    yf |= ym;
+    yd |= ym;
+    nrot += __popc(r);
+  };
+  unsigned rA, rB;
+  // steps 0 and 1: {x0, x1} with {y0, y1}, {x2, x3} with {y2, y3}
+  rA = half_step(x[0], y[0], x[1], y[1], a[0], bn[0], a[1], bn[1], act(0, 0), act(1, 1), tol2, tiny, lane);
+  rB = half_step(x[2], y[2], x[3], y[3], a[2], bn[2], a[3], bn[3], act(2, 2), act(3, 3), tol2, tiny, lane);
+  note(rA, 0, 0, 1, 1);
+  note(rB, 2, 2, 3, 3);
+  rA = half_step(x[0], y[1], x[1], y[0], a[0], bn[1], a[1], bn[0], act(0, 1), act(1, 0), tol2, tiny, lane);
+  rB = half_step(x[2], y[3], x[3], y[2], a[2], bn[3], a[3], bn[2], act(2, 3), act(3, 2), tol2, tiny, lane);
+  note(rA, 0, 1, 1, 0);
+  note(rB, 2, 3, 3, 2);
+  // steps 2 and 3: {x0, x1} with {y2, y3}, {x2, x3} with {y0, y1}
+  rA = half_step(x[0], y[2], x[1], y[3], a[0], bn[2], a[1], bn[3], act(0, 2), act(1, 3), tol2, tiny, lane);
+  rB = half_step(x[2], y[0], x[3], y[1], a[2], bn[0], a[3], bn[1], act(2, 0), act(3, 1), tol2, tiny, lane);
+  note(rA, 0, 2, 1, 3);
+  note(rB, 2, 0, 3, 1);
+  rA = half_step(x[0], y[3], x[1], y[2], a[0], bn[3], a[1], bn[2], act(0, 3), act(1, 2), tol2, tiny, lane);
+  rB = half_step(x[2], y[1], x[3], y[0], a[2], bn[1], a[3], bn[0], act(2, 1), act(3, 0), tol2, tiny, lane);
+  note(rA, 0, 3, 1, 2);
+  note(rB, 2, 1, 3, 0);
+}
+
 // One round on the 2b staged columns (local columns [0, b) = block I, [b, 2b) =
 // block J), by G = b / K warps, each holding K columns of each block in
 // registers:
@@ -442,6 +514,9 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
         return m;
       };
       unsigned r = 0;
+      if constexpr (sizeof(J) == 4 && K == 4) {
+        if (any) meet4_xor<NV>(x, y, a, bn, xf, yf, tol2, tiny, lane, xdirty, ydirty, rot);
+      } else {
       if (any) r = step_pairs<J, NV, K, 0>(x, y, a, bn, xf, yf, act_mask(0), tol2, tiny, lane);
       xdirty |= r;
       ydirty |= y_mask<K, 0>(r);
@@ -461,6 +536,7 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
         xdirty |= r;
         ydirty |= y_mask<K, 3 % K>(r);
         rot += __popc(r);
+      }
       }
 #pragma unroll
       for (int i = 0; i < K; ++i) {
