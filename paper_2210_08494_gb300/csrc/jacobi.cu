@@ -401,6 +401,51 @@ __device__ __forceinline__ void meet4_xor(Col<float, NV> (&x)[4], Col<float, NV>
   note(rB, 2, 1, 3, 0);
 }
 
+// Sum over the warp of 16 values per lane, transposed: each butterfly level
+// exchanges half of the values still held, so that lane l ends with the full sum
+// of v[l >> 1] (16 values in 16 shuffles over five levels).
+__device__ __forceinline__ float warp_sum_spread16(const float (&v)[16], int lane) {
+  constexpr unsigned F = 0xffffffffu;
+  float r8[8], r4[4], r2[2];
+  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0, h4 = (lane & 4) != 0, h2 = (lane & 2) != 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) r8[k] = (h16 ? v[k + 8] : v[k]) + __shfl_xor_sync(F, h16 ? v[k] : v[k + 8], 16);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r4[k] = (h8 ? r8[k + 4] : r8[k]) + __shfl_xor_sync(F, h8 ? r8[k] : r8[k + 4], 8);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) r2[k] = (h4 ? r4[k + 2] : r4[k]) + __shfl_xor_sync(F, h4 ? r4[k] : r4[k + 2], 4);
+  float r = (h2 ? r2[1] : r2[0]) + __shfl_xor_sync(F, h2 ? r2[0] : r2[1], 2);
+  r += __shfl_xor_sync(F, r, 1);
+  return r;
+}
+
+// Late-sweep pre-check of a meeting (FP32, four columns a side): all 16 cross
+// products from the columns as they are, one reduction, and each pair's rotation
+// test with the tracked norms.  True when no pair passes it: the meeting's steps
+// would then rotate nothing and change nothing (a rotation is the only thing
+// that changes a column), so they can be skipped with the same result.
+template <int NV>
+__device__ __forceinline__ bool meeting_clean(const Col<float, NV> (&x)[4], const Col<float, NV> (&y)[4],
+                                              const float (&a)[4], const float (&bn)[4], unsigned xf, unsigned yf,
+                                              float tol2, float tiny, int lane) {
+  float pd[16];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) pd[4 * i + j] = dot_lane(x[i], y[j]);
+  const float g = warp_sum_spread16(pd, lane);
+  const int idx = lane >> 1, me_i = idx >> 2, me_j = idx & 3;
+  float am = a[0], bm = bn[0];
+#pragma unroll
+  for (int k = 1; k < 4; ++k) {
+    if (me_i == k) am = a[k];
+    if (me_j == k) bm = bn[k];
+  }
+  const bool act = (((xf >> me_i) | (yf >> me_j)) & 1u) != 0;
+  const bool on = act && am > tiny && bm > tiny && g * g > tol2 * am * bm;
+  return __ballot_sync(0xffffffffu, on) == 0u;
+}
+
 // One round on the 2b staged columns (local columns [0, b) = block I, [b, 2b) =
 // block J), by G = b / K warps, each holding K columns of each block in
 // registers:
@@ -422,7 +467,7 @@ __device__ __forceinline__ void meet4_xor(Col<float, NV> (&x)[4], Col<float, NV>
 // Returns the number of rotations this warp applied (identical in every lane).
 template <typename J, int NV, int K>
 __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int b, int rp, int t, int sweep,
-                                             J tol2, J tiny, int lane, int wid, bool refresh) {
+                                             J tol2, J tiny, int lane, int wid, bool refresh, bool precheck) {
   const int G = b / K;  // warps doing pair work (== warps in the block)
   auto col = [&](int c) { return sm + (int64_t)c * rp; };
   auto sidx = [&](int c) { return c < b ? c : 32 + (c - b); };
@@ -515,7 +560,8 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
       };
       unsigned r = 0;
       if constexpr (sizeof(J) == 4 && K == 4) {
-        if (any) meet4_xor<NV>(x, y, a, bn, xf, yf, tol2, tiny, lane, xdirty, ydirty, rot);
+        if (any && !(precheck && meeting_clean<NV>(x, y, a, bn, xf, yf, tol2, tiny, lane)))
+          meet4_xor<NV>(x, y, a, bn, xf, yf, tol2, tiny, lane, xdirty, ydirty, rot);
       } else {
       if (any) r = step_pairs<J, NV, K, 0>(x, y, a, bn, xf, yf, act_mask(0), tol2, tiny, lane);
       xdirty |= r;
@@ -743,6 +789,10 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
 
   bool converged = false;
   int sweep = 0, last_t = 0;
+  // late sweeps (the previous one rotated fewer than 1 in 8 pairs) pre-check
+  // each meeting and skip it when it would rotate nothing
+  const int64_t npairs = (int64_t)P.cols * (P.cols - 1) / 2;
+  int prev_total = -1;
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) s_rot = 0;
     for (int t = 0; t < nblk - 1; ++t) {
@@ -763,7 +813,8 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
       // with the DSM exchange the tracked norms travel with the blocks and are refreshed
       // once per sweep; through L2 they are recomputed every round
       const int rot = process_round<J, NV, PairK<J, NV>::K>(sm, s_nrm[DSM ? cur : 0], st, b, rp, t, sweep, tol2,
-                                                            tiny, lane, wid, !DSM || t == 0);
+                                                            tiny, lane, wid, !DSM || t == 0,
+                                                            prev_total >= 0 && (int64_t)prev_total * 8 < npairs);
       if (lane == 0 && rot) atomicAdd(&s_rot, rot);
       last_t = t;
       if (!DSM) {
@@ -836,6 +887,7 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
       converged = true;
       break;
     }
+    prev_total = s_total;
   }
   if (DSM && !s_stop) {
     // write the final blocks back: after the last round's exchange, buffer `cur`
