@@ -446,6 +446,21 @@ __device__ __forceinline__ bool meeting_clean(const Col<float, NV> (&x)[4], cons
   return __ballot_sync(0xffffffffu, on) == 0u;
 }
 
+// The same pre-check for two columns a side (FP64, or FP32 on tall problems):
+// four cross products, one reduction.
+template <typename J, int NV>
+__device__ __forceinline__ bool meeting_clean2(const Col<J, NV> (&x)[2], const Col<J, NV> (&y)[2],
+                                               const J (&a)[2], const J (&bn)[2], unsigned xf, unsigned yf, J tol2,
+                                               J tiny, int lane) {
+  const J pd[4] = {dot_lane(x[0], y[0]), dot_lane(x[0], y[1]), dot_lane(x[1], y[0]), dot_lane(x[1], y[1])};
+  const J g = warp_sum_spread<J, 4>(pd, lane);  // lane l: pair l / 8
+  const int idx = lane >> 3, i = idx >> 1, j = idx & 1;
+  const J am = i ? a[1] : a[0], bm = j ? bn[1] : bn[0];
+  const bool act = (((xf >> i) | (yf >> j)) & 1u) != 0;
+  const bool on = act && am > tiny && bm > tiny && g * g > tol2 * am * bm;
+  return __ballot_sync(0xffffffffu, on) == 0u;
+}
+
 // One round on the 2b staged columns (local columns [0, b) = block I, [b, 2b) =
 // block J), by G = b / K warps, each holding K columns of each block in
 // registers:
@@ -563,22 +578,24 @@ __device__ __forceinline__ int process_round(J* sm, J* s_nrm, int* s_stamp, int 
         if (any && !(precheck && meeting_clean<NV>(x, y, a, bn, xf, yf, tol2, tiny, lane)))
           meet4_xor<NV>(x, y, a, bn, xf, yf, tol2, tiny, lane, xdirty, ydirty, rot);
       } else {
-      if (any) r = step_pairs<J, NV, K, 0>(x, y, a, bn, xf, yf, act_mask(0), tol2, tiny, lane);
+      bool live = any;
+      if constexpr (K == 2) live = any && !(precheck && meeting_clean2<J, NV>(x, y, a, bn, xf, yf, tol2, tiny, lane));
+      if (live) r = step_pairs<J, NV, K, 0>(x, y, a, bn, xf, yf, act_mask(0), tol2, tiny, lane);
       xdirty |= r;
       ydirty |= y_mask<K, 0>(r);
       rot += __popc(r);
       if (K > 1) {
-        r = any ? step_pairs<J, NV, K, 1 % K>(x, y, a, bn, xf, yf, act_mask(1 % K), tol2, tiny, lane) : 0u;
+        r = live ? step_pairs<J, NV, K, 1 % K>(x, y, a, bn, xf, yf, act_mask(1 % K), tol2, tiny, lane) : 0u;
         xdirty |= r;
         ydirty |= y_mask<K, 1 % K>(r);
         rot += __popc(r);
       }
       if (K > 2) {
-        r = any ? step_pairs<J, NV, K, 2 % K>(x, y, a, bn, xf, yf, act_mask(2 % K), tol2, tiny, lane) : 0u;
+        r = live ? step_pairs<J, NV, K, 2 % K>(x, y, a, bn, xf, yf, act_mask(2 % K), tol2, tiny, lane) : 0u;
         xdirty |= r;
         ydirty |= y_mask<K, 2 % K>(r);
         rot += __popc(r);
-        r = any ? step_pairs<J, NV, K, 3 % K>(x, y, a, bn, xf, yf, act_mask(3 % K), tol2, tiny, lane) : 0u;
+        r = live ? step_pairs<J, NV, K, 3 % K>(x, y, a, bn, xf, yf, act_mask(3 % K), tol2, tiny, lane) : 0u;
         xdirty |= r;
         ydirty |= y_mask<K, 3 % K>(r);
         rot += __popc(r);
