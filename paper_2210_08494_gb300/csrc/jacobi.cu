@@ -461,6 +461,91 @@ __device__ __forceinline__ bool meeting_clean2(const Col<J, NV> (&x)[2], const C
   return __ballot_sync(0xffffffffu, on) == 0u;
 }
 
+// Convergence check after a sweep that rotated few pairs (FP32, four columns
+// per warp).  Every column of the problem is in W (global memory) and `stamp`
+// holds the sweep of each column's last rotation.  The next sweep would test
+// exactly the pairs with a column rotated in sweep `sweep` ("fresh" ones): this
+// CTA tests its own 2b staged columns (sm, column c at sm + c rp, global index
+// gidx(c)) against every fresh column, 4 x 4 products per reduction, with norms
+// recomputed from the columns as the next sweep's refresh would.  Returns true
+// (in every thread) when some pair would rotate.
+template <int NV, typename GIdx>
+__device__ bool fresh_pairs_open(const float* sm, int b, int rp, GIdx gidx, const float* W, const int* stamp,
+                                 int cols, int sweep, float tol2, float tiny, int* s_list, int* s_count,
+                                 float* s_own_nrm, int lane, int wid, int nwarps) {
+  // the fresh columns, compacted (order does not matter)
+  if (threadIdx.x == 0) *s_count = 0;
+  __syncthreads();
+  for (int g = threadIdx.x; g < cols; g += blockDim.x)
+    if (stamp[g] == sweep) s_list[atomicAdd(s_count, 1)] = g;
+  // own column norms
+  for (int c = wid; c < 2 * b; c += nwarps) {
+    Col<float, NV> x;
+    x.load(sm + (int64_t)c * rp, lane);
+    const float t = warp_sum_j(dot_lane(x, x));
+    if (lane == 0) s_own_nrm[c] = t;
+  }
+  __syncthreads();
+  const int nf = *s_count;
+  bool open = false;
+  const int ngrp = (nf + 3) / 4, nown = (2 * b + 3) / 4;
+  for (int q = wid; q < ngrp * nown && !open; q += nwarps) {
+    const int fg = q / nown, og = q - fg * nown;
+    Col<float, NV> f[4], x[4];
+    float fa[4], xa[4];
+    int fgi[4], xgi[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = 4 * fg + i, c = 4 * og + i;
+      fgi[i] = k < nf ? s_list[k] : -1;
+      xgi[i] = c < 2 * b ? gidx(c) : -2;
+      if (fgi[i] >= 0) {
+        f[i].load(W + (int64_t)fgi[i] * rp, lane);
+      } else {
+#pragma unroll
+        for (int e = 0; e < Col<float, NV>::P; ++e) f[i].v[e] = 0;
+      }
+      if (c < 2 * b) {
+        x[i].load(sm + (int64_t)c * rp, lane);
+        xa[i] = s_own_nrm[c];
+      } else {
+#pragma unroll
+        for (int e = 0; e < Col<float, NV>::P; ++e) x[i].v[e] = 0;
+        xa[i] = 0.f;
+      }
+    }
+    float fn[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) fn[i] = dot_lane(f[i], f[i]);
+    const float fsum = warp_sum_spread<float, 4>(fn, lane);  // lane l: fresh column l / 8
+#pragma unroll
+    for (int i = 0; i < 4; ++i) fa[i] = __shfl_sync(0xffffffffu, fsum, 8 * i);
+    float pd[16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pd[4 * i + j] = dot_lane(x[i], f[j]);
+    const float g = warp_sum_spread16(pd, lane);
+    const int idx = lane >> 1, me_i = idx >> 2, me_j = idx & 3;
+    float am = xa[0], bm = fa[0];
+    int gi = xgi[0], gj = fgi[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+      if (me_i == k) {
+        am = xa[k];
+        gi = xgi[k];
+      }
+      if (me_j == k) {
+        bm = fa[k];
+        gj = fgi[k];
+      }
+    }
+    const bool on = gj >= 0 && gi >= 0 && gi != gj && am > tiny && bm > tiny && g * g > tol2 * am * bm;
+    open = __ballot_sync(0xffffffffu, on) != 0u;
+  }
+  return __syncthreads_or(open) != 0;
+}
+
 // One round on the 2b staged columns (local columns [0, b) = block I, [b, 2b) =
 // block J), by G = b / K warps, each holding K columns of each block in
 // registers:
@@ -756,6 +841,8 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
   __shared__ int s_abort[2];
   __shared__ int s_total;
   __shared__ int s_stop;
+  __shared__ int s_vopen;  // the convergence check found a pair that would rotate (this CTA)
+  __shared__ int s_vany;   // ... in some CTA of the cluster
   __shared__ double s_tiny;
   __shared__ __align__(16) J s_nrm[3][64];      // tracked squared norms of the staged columns (per buffer)
   __shared__ __align__(16) int s_stamp[3][64];  // sweep of each staged column's last rotation (per buffer)
@@ -905,6 +992,44 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
       break;
     }
     prev_total = s_total;
+    // few rotations: instead of a sweep that would only confirm convergence, write
+    // the columns back and test the pairs of the columns this sweep rotated
+    if constexpr (DSM && sizeof(J) == 4 && PairK<J, NV>::K == 4) {
+      if ((int64_t)s_total * 256 <= npairs && sweep + 1 < max_sweeps) {
+        const int tn = last_t + 1;
+        const int vI = circle_pos(crank, tn, nblk), vJ = circle_pos(nblk - 1 - crank, tn, nblk);
+        const J* smv = buffer(cur);
+        copy_vecs(reinterpret_cast<V*>(W + (int64_t)vI * b * rp), reinterpret_cast<const V*>(smv), nvec, tid, nthr);
+        copy_vecs(reinterpret_cast<V*>(W + (int64_t)vJ * b * rp), reinterpret_cast<const V*>(smv + (int64_t)b * rp),
+                  nvec, tid, nthr);
+        for (int c = tid; c < 2 * b; c += nthr)
+          stamp[c < b ? vI * b + c : vJ * b + (c - b)] = s_stamp[cur][c < b ? c : 32 + (c - b)];
+        cluster.sync();  // every CTA's columns and stamps are in global memory
+        // scratch in the buffer after `cur` (free until the next sweep's first push)
+        int* s_list = reinterpret_cast<int*>(buffer(cur == 2 ? 0 : cur + 1));
+        int* s_cnt_f = s_list + P.cols_pad;
+        float* s_own = reinterpret_cast<float*>(s_cnt_f + 32);
+        auto gidx = [&](int c) { return c < b ? vI * b + c : vJ * b + (c - b); };
+        const bool open = fresh_pairs_open<NV>(reinterpret_cast<const float*>(smv), b, rp, gidx,
+                                               reinterpret_cast<const float*>(W), stamp, P.cols, sweep,
+                                               (float)tol2, (float)tiny, s_list, s_cnt_f, s_own, lane, wid,
+                                               nthr / 32);
+        if (tid == 0) s_vopen = open ? 1 : 0;
+        cluster.sync();
+        if (tid == 0) {
+          int any = 0;
+          for (int q = 0; q < C; ++q) any |= *cluster.map_shared_rank(&s_vopen, q);
+          s_vany = any;
+        }
+        __syncthreads();
+        const bool still_open = s_vany != 0;
+        cluster.sync();  // every CTA has read the verdicts before s_vopen changes again
+        if (!still_open) {  // nothing would rotate: converged after this sweep
+          converged = true;
+          break;
+        }
+      }
+    }
   }
   if (DSM && !s_stop) {
     // write the final blocks back: after the last round's exchange, buffer `cur`
