@@ -994,19 +994,39 @@ __global__ void __launch_bounds__(PairK<J, NV>::kMaxThreads) jacobi_kernel(const
     prev_total = s_total;
     // few rotations: instead of a sweep that would only confirm convergence, write
     // the columns back and test the pairs of the columns this sweep rotated
-    if constexpr (DSM && sizeof(J) == 4 && PairK<J, NV>::K == 4) {
+    if constexpr (sizeof(J) == 4 && PairK<J, NV>::K == 4) {
       if ((int64_t)s_total * 256 <= npairs && sweep + 1 < max_sweeps) {
-        const int tn = last_t + 1;
-        const int vI = circle_pos(crank, tn, nblk), vJ = circle_pos(nblk - 1 - crank, tn, nblk);
-        const J* smv = buffer(cur);
-        copy_vecs(reinterpret_cast<V*>(W + (int64_t)vI * b * rp), reinterpret_cast<const V*>(smv), nvec, tid, nthr);
-        copy_vecs(reinterpret_cast<V*>(W + (int64_t)vJ * b * rp), reinterpret_cast<const V*>(smv + (int64_t)b * rp),
-                  nvec, tid, nthr);
-        for (int c = tid; c < 2 * b; c += nthr)
-          stamp[c < b ? vI * b + c : vJ * b + (c - b)] = s_stamp[cur][c < b ? c : 32 + (c - b)];
+        int vI, vJ;
+        J* smv;
+        int* s_list;
+        if constexpr (DSM) {
+          // this CTA's blocks (those of the round after the last) and their stamps
+          // go back to global memory; scratch in the buffer after `cur` (free until
+          // the next sweep's first push)
+          const int tn = last_t + 1;
+          vI = circle_pos(crank, tn, nblk);
+          vJ = circle_pos(nblk - 1 - crank, tn, nblk);
+          smv = buffer(cur);
+          copy_vecs(reinterpret_cast<V*>(W + (int64_t)vI * b * rp), reinterpret_cast<const V*>(smv), nvec, tid,
+                    nthr);
+          copy_vecs(reinterpret_cast<V*>(W + (int64_t)vJ * b * rp),
+                    reinterpret_cast<const V*>(smv + (int64_t)b * rp), nvec, tid, nthr);
+          for (int c = tid; c < 2 * b; c += nthr)
+            stamp[c < b ? vI * b + c : vJ * b + (c - b)] = s_stamp[cur][c < b ? c : 32 + (c - b)];
+          s_list = reinterpret_cast<int*>(buffer(cur == 2 ? 0 : cur + 1));
+        } else {
+          // through L2 the columns and stamps are in global memory after every round:
+          // stage the blocks of the next sweep's first round; scratch after the buffer
+          vI = circle_pos(crank, 0, nblk);
+          vJ = circle_pos(nblk - 1 - crank, 0, nblk);
+          smv = buffer(0);
+          copy_vecs(reinterpret_cast<V*>(smv), reinterpret_cast<const V*>(W + (int64_t)vI * b * rp), nvec, tid,
+                    nthr);
+          copy_vecs(reinterpret_cast<V*>(smv + (int64_t)b * rp), reinterpret_cast<const V*>(W + (int64_t)vJ * b * rp),
+                    nvec, tid, nthr);
+          s_list = reinterpret_cast<int*>(smv + (int64_t)2 * b * rp);
+        }
         cluster.sync();  // every CTA's columns and stamps are in global memory
-        // scratch in the buffer after `cur` (free until the next sweep's first push)
-        int* s_list = reinterpret_cast<int*>(buffer(cur == 2 ? 0 : cur + 1));
         int* s_cnt_f = s_list + P.cols_pad;
         float* s_own = reinterpret_cast<float*>(s_cnt_f + 32);
         auto gidx = [&](int c) { return c < b ? vI * b + c : vJ * b + (c - b); };
@@ -1152,6 +1172,10 @@ int launch_jacobi(const JacobiProblem* probs, int nprob, int C, DType j_t, doubl
   return launch_jacobi_mode(probs, nprob, C, j_t, tol, max_sweeps, dsm != 0, s);
 }
 
+// scratch of the few-rotation convergence check when the blocks go through L2:
+// the list of rotated columns, a counter, the staged columns' norms
+static size_t jacobi_check_scratch(int cols_pad) { return (size_t)(cols_pad + 32 + 64) * 4; }
+
 int launch_jacobi_mode(const JacobiProblem* probs, int nprob, int C, DType j_t, double tol, int max_sweeps,
                        bool want_dsm, cudaStream_t s) {
   if (nprob <= 0) return 0;
@@ -1177,8 +1201,11 @@ int launch_jacobi_mode(const JacobiProblem* probs, int nprob, int C, DType j_t, 
   if (j_t == DT_F64)
     return dsm ? launch_nv<double, true>(batch, nprob, C, b, rp, 3 * smem, tol, max_sweeps, s)
                : launch_nv<double, false>(batch, nprob, C, b, rp, smem, tol, max_sweeps, s);
+  int cp_max = 0;
+  for (int i = 0; i < nprob; ++i) cp_max = std::max(cp_max, probs[i].cols_pad);
   return dsm ? launch_nv<float, true>(batch, nprob, C, b, rp, 3 * smem, tol, max_sweeps, s)
-             : launch_nv<float, false>(batch, nprob, C, b, rp, smem, tol, max_sweeps, s);
+             : launch_nv<float, false>(batch, nprob, C, b, rp, smem + jacobi_check_scratch(cp_max), tol,
+                                       max_sweeps, s);
 }
 
 int launch_wait_selftest(long long limit_cycles, int* out, cudaStream_t s) {
@@ -1190,5 +1217,6 @@ int launch_wait_selftest(long long limit_cycles, int* out, cudaStream_t s) {
 size_t jacobi_smem_bytes(int b, int rows_pad, DType j_t) {
   return (size_t)2 * b * rows_pad * (j_t == DT_F64 ? 8 : 4);
 }
+
 
 }  // namespace bkfac
