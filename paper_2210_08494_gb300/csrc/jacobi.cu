@@ -194,13 +194,17 @@ __device__ __forceinline__ void rotate_lane(Col<double, NV>& x, Col<double, NV>&
 // which the squared norms move: a' = a - t g, b' = b + t g.
 //
 // FP32: a scale-free closed form on the hardware approximations.  With
-// d = (b - a)/(a + b) and h = 2 g/(a + b) (both in [-1, 1]), R = sqrt(d^2 + h^2)
+// d = (b - a) s and h = 2 g s for a power of two s ~ 1/(a + b) (the formulas
+// below depend only on the ratio h / d), R = sqrt(d^2 + h^2)
 // and u = |d| + R:  cos = u / sqrt(2 R u),  sin = sign(d) h / sqrt(2 R u),
 // tan = sign(d) h / u -- three dependent approximations (rsqrt, rsqrt,
 // reciprocal) where the cotangent form needs five.  The angle need not be
 // exact; the tau form above keeps the applied rotation orthogonal.
 __device__ __forceinline__ void rotation_params(float a, float b, float g, float& s, float& tau, float& tg) {
-  const float rab = __fdividef(1.0f, a + b);
+  // d and h scaled by a power of two (from the exponent of a + b) into [-2, 2]:
+  // exact, and no reciprocal on the step's dependency chain
+  const int ex = min((__float_as_int(a + b) >> 23) & 0xff, 253);
+  const float rab = __int_as_float((253 - ex) << 23);  // (a + b) rab in [0.5, 1)
   const float d = (b - a) * rab, h = 2.0f * g * rab;
   const float q = fmaf(d, d, h * h);
   const float R = q * rsqrtf(q);
