@@ -337,10 +337,15 @@ int bkfac_apply_noalloc(const bkfac_factor* fA, const bkfac_factor* fG, double l
 /* Diagnostics for tests: byte offsets, inside an update workspace, of the
  * intermediates left by the last bkfac_init / bkfac_update that used it:
  *   out[0] M (r_cur_old x n, column-major, dtype of U)
- *   out[1] Q (d x n, column-major, ld = out[6]; P before the QR)
- *   out[2] R (n x n, column-major, double; R = R2 R1)
+ *   out[1] Q (d x n, column-major, ld = out[6])
+ *   out[2] the eigensolve's matrix (the core factor's columns, padded, in the
+ *          eigensolve's precision; after the update its converged columns)
  *   out[3] lambda (N = r_cur_old + n doubles, descending, before truncation)
- *   out[4] N (core size), out[5] leading dimension of M, out[6] ld of Q.
+ *   out[4] P (d x n, column-major, ld = out[6]: the residual before its QR)
+ *   out[5] leading dimension of M, out[6] leading dimension of Q and P.
+ *   out[7] the eigensolve's counters (int32): [0] the full sweeps it ran (a
+ *          closing check that finds no pair left to rotate is not a sweep),
+ *          [1 + s] the rotations applied in sweep s (s < 48).
  * r_cur_old is the factor's r_cur before the update.  Returns BKFAC_EINVAL
  * for the dense path (which has no M, Q, R). */
 int bkfac_debug_offsets(const bkfac_factor* f, int n, int64_t out[8]);
