@@ -228,6 +228,9 @@ struct ApplyPlan {
   int64_t ld1, ld2, ldw;
   size_t o_T1, o_T2, o_T3, o_W1, o_part, o_part1, o_cA, o_cG, o_cAo, o_cGo, o_alpha, total;
   size_t part1_bytes;
+  // the FP32 pass 1's split-K scratch: the small products' region and part1, which
+  // lie back to back and are free while pass 1 runs
+  size_t o_pass1, pass1_bytes;
   // mixed path on the TMA-fed tensor cores: BF16 K-major copies of the operands
   bool tma;
   int64_t ldgb, ldgt, ldua, ldug, ld2k;  // row pitches (elements) of Gb, Gt, UAb, UGb, A2 / B2
@@ -260,6 +263,8 @@ ApplyPlan plan_apply(const bkfac_factor* fA, const bkfac_factor* fG, int kA, int
   // pass 1 may split K in two: scratch for two copies of the larger of T1 / T2
   p.part1_bytes = (size_t)2 * std::max((size_t)p.dG * rA, (size_t)p.dA * rG) * aes;
   p.o_part1 = L.add(p.part1_bytes);
+  p.o_pass1 = p.o_part;
+  p.pass1_bytes = p.o_part1 + p.part1_bytes - p.o_part;
   p.o_cA = L.add((size_t)rA * 8);
   p.o_cG = L.add((size_t)rG * 8);
   p.o_cAo = L.add((size_t)rA * 8);
@@ -1231,8 +1236,9 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.tf32x3 = pr.x3;
     g.C = T1;
     g.ldc = cap.ld1;
-    g.partial = at<void>(ws, cap.o_part1);
-    g.partial_bytes = cap.part1_bytes;
+    // (3xTF32 products keep pass 1's own scratch: more splits measured slower there)
+    g.partial = at<void>(ws, pr.x3 ? cap.o_part1 : cap.o_pass1);
+    g.partial_bytes = pr.x3 ? cap.part1_bytes : cap.pass1_bytes;
     PHASE(PH_APPLY1, gemm_run(g, pr.t, pr.acc, pr.t, s));
   }
   if (kG > 0 && !cap.tma) {
@@ -1251,8 +1257,9 @@ int bkfac_apply(const bkfac_factor* fA, const bkfac_factor* fG, double lamA, dou
     g.C = T2;  // column-major d_in x kG == row-major kG x d_in
     g.ldc = cap.ld2;
     g.cs = cGo;
-    g.partial = at<void>(ws, cap.o_part1);
-    g.partial_bytes = cap.part1_bytes;
+    // (3xTF32 products keep pass 1's own scratch: more splits measured slower there)
+    g.partial = at<void>(ws, pr.x3 ? cap.o_part1 : cap.o_pass1);
+    g.partial_bytes = pr.x3 ? cap.part1_bytes : cap.pass1_bytes;
     PHASE(PH_APPLY1, gemm_run(g, pr.t, pr.acc, pr.t, s));
   }
   // small: T3' = diag(C_G) (U_G^T T1) diag(C_A);  W1 = T1 diag(C_A / lamG') + U_G T3'
