@@ -9,19 +9,26 @@
 // would square the condition number).  The same kernel serves the dense path
 // (W = [U sqrt(rho sigma), sqrt(c) X], d rows) and re-orthonormalisation.
 //
-// Parallel layout: one thread-block cluster of C CTAs per problem.  The
-// columns are split into 2C blocks of b columns; a round-robin tournament
-// over the blocks (circle method) meets every block pair once per sweep in
-// 2C - 1 rounds, CTA c working on one block pair per round in shared memory.
-// Between rounds the blocks go back to global memory (L2-resident) and the
-// cluster synchronises with the hardware cluster barrier; no CTA spins on a
-// flag.  Inside a CTA there is one warp per column of the first block
-// (blockDim = 32 b, b <= 16): in sub-round s warp q rotates its column against column
-// (q + s) mod b of the second block, so all b pairs of a sub-round are in
-// flight at once.  A lane holds rows {lane, lane + 32, ...} of its pair in
-// registers (16-byte vector loads); the warp's own column stays in registers
-// for the whole round.  The sweep count is capped; a problem that reaches the
-// cap reports BKFAC_ENOCONV and still returns its current columns.
+// Parallel layout: one thread-block cluster of C CTAs per problem (a grouped
+// launch runs one cluster per problem).  The columns are split into 2C blocks
+// of b columns; a round-robin tournament over the blocks (circle method) meets
+// every block pair once per sweep in 2C - 1 rounds, CTA c holding two blocks
+// per round in shared memory.  Between rounds the blocks move to their next
+// holders either by bulk copies over distributed shared memory (three buffers,
+// completion on the receiver's mbarrier, a split cluster barrier) or, when
+// three buffers do not fit or a group runs more clusters than the GPU holds,
+// through global memory (L2) and the cluster barrier.  Inside a CTA each warp
+// keeps K columns of the first block in registers for the whole round (K = 4
+// for FP32 up to 512 rows, else 2) and meets the K-column groups of the second
+// block in turn; a lane holds the 16-byte vectors lane, lane + 32, ... of each
+// column (rows 4 lane .. 4 lane + 3, + 128, ... in FP32, kept as packed pairs
+// for the two-wide FMA; two rows per vector in FP64).  The
+// pairs of a meeting run as steps of K disjoint pairs with one spread warp
+// reduction per step (FP32, K = 4: two interleaved chains of two pairs on the
+// XOR schedule).  Late sweeps skip meetings that would rotate nothing, and a
+// sweep that rotated few pairs is followed by a check of the pairs it left
+// open instead of a full sweep.  The sweep count is capped; a problem that
+// reaches the cap reports BKFAC_ENOCONV and still returns its current columns.
 #include <cooperative_groups.h>
 
 #include <algorithm>
