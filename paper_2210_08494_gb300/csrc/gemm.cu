@@ -7,9 +7,15 @@
 // fused scaling epilogue.  Long-K products with a small output use split-K:
 // each split writes its partial tile, and a second kernel sums the splits in a
 // fixed order (deterministic, independent of scheduling) and applies the
-// epilogue.  In FP32 mode the Gram takes FP32 operands and accumulates in
-// FP64 (products of two floats are exact in double).  In mixed mode the
-// operands are rounded to BF16 on load and accumulate in FP32.
+// epilogue (tall column-major outputs through transposing 32 x 128 tiles).
+// A 128 x 128 tile kernel serves the large FP32 products; the choice of kernel
+// and K splits per product shape is the autotuner's when it has timed that
+// shape (tune.cu), else a heuristic sized by the SM count.  The Gram of FP32
+// data for CholeskyQR is FP64-accurate on the FP32 pipe (exact products and
+// TwoSum compensation, summed in FP64 across splits); an FP64-accumulating
+// variant of the template serves the remaining FP32-in / FP64-out products.
+// Operands rounded to BF16 on load (mixed mode) when a product does not go to
+// the tensor cores.
 #include <algorithm>
 
 #include "common.cuh"
